@@ -1,0 +1,16 @@
+"""FP64 CPU oracle for the split-preconditioned fixed-point iteration.
+
+TEST INFRASTRUCTURE, not part of the product.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import, call or execute anything here.  It shares no code with the CUDA path.
+
+Modules:
+  dft         the DFT by its definition (dense matrices, loops)
+  usp_oracle  Algorithm 1 with the forward-eliminated operator, FP64
+  canon       canonical form (smallest circle, scaling) for Helmholtz and
+              diffusion problems
+  dense       the operators as dense matrices for brute-force checks
+
+Every function pinned by a ``-m "not gpu"`` test; none is marked
+"parity unpinned".
+"""
