@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the split-preconditioned fixed-point solver on one GB300.
+
+Workload: the 3-D Helmholtz medium of size 256^3 (refractive index 1-1.5
+from a seeded smoothed random field, sigma 6 px, plus spheres of n = 1.45,
+absorbing layer 32 px per face, Gaussian beam source), pixel = lambda/4,
+complex64, solved to a relative preconditioned residual of 1e-6.
+
+One step = create the solver (validation, alpha, scratch) + solve to 1e-6
+(reference norm, iterations, FP64 refinement) + destroy, inputs resident in
+HBM.  `value` = iterations per second over the timed steps (all ranks);
+`ms_per_step` = seconds to residual 1e-6 per solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+reference arm: there is no reference implementation, only the paper).
+Multi-GPU runs are independent replicas (the solve does not shard).
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "256³ Helmholtz: s to residual 1e-6, iter/s, % HBM roofline; plain vs chosen"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--workload", default="helmholtz", choices=["helmholtz", "diffusion"])
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--maxit", type=int, default=20000)
+    p.add_argument("--schedule", type=int, default=0)
+    p.add_argument("--plain", action="store_true", help="time the plain FP32 iteration")
+    p.add_argument("--cpu-iters", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, plain and roofline legs")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args, seed=0):
+    from paper_2207_14222_gb300 import inputs
+    if args.workload == "helmholtz":
+        return inputs.helmholtz_3d(args.n, seed=seed)
+    return inputs.diffusion_3d(args.n, seed=seed)
+
+
+def workload_name(args):
+    return "%s3d_%d" % (args.workload, args.n)
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, n = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            n += 1
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------- roofline ---
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_14222_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/, valid
+    only if the kernel sources are unchanged since (line format:
+    `bench-traffic: <pass> <bytes per launch> <sources sha>`)."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    sha = kernel_sources_sha()
+    for f in sorted(os.listdir(d)):
+        if not f.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(d, f)):
+            m = re.match(r"\s*bench-traffic:\s*(\S+)\s+([0-9.eE+]+)\s+(\S+)", line)
+            if m and m.group(1) == kernel and m.group(3) == sha:
+                return float(m.group(2))
+    return None
+
+
+# ------------------------------------------------------------ our arm ---
+
+def run_ours(args):
+    import torch
+    from paper_2207_14222_gb300 import canon
+    from paper_2207_14222_gb300.solver import Solver, kernel_launches
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    prob = workload(args)
+    cf = canon.canonical(prob)
+    shape = cf["V"].shape
+    V = torch.from_numpy(cf["V"]).to(dev)
+    y = torch.from_numpy(cf["y"]).to(dev)
+    x = torch.empty_like(y)
+
+    def step():
+        with Solver(shape, cf["a"], cf["b"], V, plain=args.plain, schedule=args.schedule) as s:
+            _, r = s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
+        return r
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_smi_id(torch, dev))
+    sampler.start()
+    l0 = kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = [step() for _ in range(args.steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    iters = sum(r["iterations"] for r in res)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        c = torch.tensor([iters], device=dev, dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        iters_all = int(c.item())
+    else:
+        iters_all = iters
+    value = iters_all / (elapsed_ms / 1e3)
+    ms_per_step = elapsed_ms / args.steps
+
+    extras = {}
+    if not args.no_extras:
+        extras = extras_legs(args, torch, dev, cf, V, y, shape, Solver, res[-1]["iterations"])
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, prob)
+
+    if rank == 0:
+        last = res[-1]
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "iter/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": workload_name(args),
+                "grid": list(shape),
+                "tol": args.tol,
+                "mode": "plain" if args.plain else "fp32+fp64-refinement",
+                "schedule": ["auto", "pencil", "fused"][args.schedule],
+                "step": "create + solve to tol + destroy",
+                "l2": "inputs 384 MiB > L2, no flush",
+                "replicas": ws,
+            },
+            "s_to_residual": ms_per_step / 1e3,
+            "iterations": last["iterations"],
+            "refinements": last["refinements"],
+            "final_rel_residual": last["final_rel_residual"],
+            "converged": bool(last["converged"]),
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        line.update(extras)
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
+    out = {}
+    # per-kernel durations (CUDA events on the solver's stream) -> roofline
+    xt = torch.empty_like(y)
+    with Solver(shape, cf["a"], cf["b"], V, schedule=args.schedule) as s:
+        s.solve(y, x=xt, tol=0.0, maxit=5)  # warm
+        passes = s.time_passes(y, xt, iters=20)
+    per_it_ms = sum(p["ms"] for p in passes)
+    dom = max(passes, key=lambda p: p["ms"])
+    peak, kind = measured_hbm_peak()
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    out["roofline"] = {
+        "bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+        "unit": "GB/s", "frac": achieved / peak, "peak_source": kind,
+        "traffic": recorded_traffic(dom["name"]),
+        "bytes_per_launch": dom["bytes"], "ms_per_launch": dom["ms"],
+        "iteration_ms": per_it_ms,
+        "iteration_frac": sum(p["bytes"] for p in passes) / (per_it_ms * 1e-3) / 1e9 / peak,
+        "passes": [{"name": p["name"], "ms": round(p["ms"], 5),
+                    "GBps": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)} for p in passes],
+    }
+    # end to end through the host API: pinned V, y in; x out
+    Vh = V.cpu().pin_memory()
+    yh = y.cpu().pin_memory()
+    xh = torch.empty_like(yh).pin_memory()
+    t_it, t_s = 0, 0.0
+    steps = max(1, min(args.steps, 3))
+    for k in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Vd = Vh.to(dev, non_blocking=True)
+        with Solver(shape, cf["a"], cf["b"], Vd, plain=args.plain, schedule=args.schedule) as s:
+            _, r = s.solve_host(yh, xh, tol=args.tol, maxit=args.maxit)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        del Vd
+        if k > 0:  # first one is warm-up
+            t_it += r["iterations"]
+            t_s += dt
+    out["e2e"] = {"value": t_it / t_s, "unit": "iter/s",
+                  "h2d_bytes_per_step": int(Vh.numel() * Vh.element_size() + yh.numel() * 8),
+                  "d2h_bytes_per_step": int(xh.numel() * 8),
+                  "s_per_solve": t_s / steps}
+    # plain Algorithm 1 (no refinement) on the same problem: its FP32 floor
+    if not args.plain:
+        xp = torch.empty_like(y)
+        with Solver(shape, cf["a"], cf["b"], V, plain=True, schedule=args.schedule) as s:
+            maxit = 4 * max(ref_iters, 250)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r = s.solve(y, x=xp, tol=args.tol, maxit=maxit)
+            dt = time.perf_counter() - t0
+            h = s.history()
+        out["plain"] = {"reached_tol": bool(r["converged"]), "iterations": r["iterations"],
+                        "min_rel_residual": float(h.min()), "argmin": int(h.argmin()) + 1,
+                        "iter_per_s": r["iterations"] / dt,
+                        "s_to_min_residual": dt * (int(h.argmin()) + 1) / r["iterations"]}
+    return out
+
+
+# ------------------------------------------------------ CPU (oracle) arm ---
+
+def _oracle_setup(prob):
+    from oracle import canon as ocanon
+    from oracle import usp_oracle as uo
+    cf = ocanon.canonical(prob)
+    Lh = uo.lhat(cf["V"].shape, cf["dx"], cf["a"], cf["b"])
+    return cf, Lh, uo
+
+
+def cpu_baseline(args, prob, iters=None):
+    """The FP64 oracle as it stands, a bounded sample of the same workload."""
+    iters = iters or args.cpu_iters
+    cf, Lh, uo = _oracle_setup(prob)
+    alpha = uo.alpha_star(cf["V"])
+    t0 = time.perf_counter()
+    uo.iterate(cf["V"], cf["y"], Lh, alpha, iters, ref_norm=1.0)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": "%d iterations of Algorithm 1 on the %s workload, FP64 NumPy "
+                      "(single-threaded FFT), setup untimed" % (iters, workload_name(args))}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    prob = workload(args)
+    cf, Lh, uo = _oracle_setup(prob)
+    alpha = uo.alpha_star(cf["V"])
+    x = np.zeros_like(cf["y"])
+    for _ in range(max(args.warmup, 0)):
+        x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, 1, x0=x, ref_norm=1.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, 1, x0=x, ref_norm=1.0)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "grid": [args.n] * 3, "tol": args.tol,
+                   "step": "one iteration of the FP64 CPU oracle (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d timed iterations of Algorithm 1 (FP64 NumPy oracle) on "
+                                   "the %s workload" % (args.steps, workload_name(args))},
+        "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * usp.h -- C ABI of the GB300 (sm_103a) solver for the fixed-point
+ * (Richardson) iteration with the universal split preconditioner
+ * (Vettenburg & Vellekoop, "A universal matrix-free split preconditioner for
+ * the fixed-point iterative solution of non-symmetric linear systems").
+ *
+ * The problem is a canonical linear system A x = y with A = L + V (Sec. 2):
+ *   - L is translation invariant on a periodic grid, given by its Fourier
+ *     symbol  Lhat(p) = a |p|^2 + b,  p = 2 pi m / (n dx), m the FFT-order
+ *     frequency index on each axis;
+ *   - V is a pointwise potential with max |V| < 1;
+ *   - A is accretive (Eq. accretivity-condition).
+ * The solver runs Algorithm 1 on the forward-eliminated operator (Sec. 2.1)
+ *     Delta = B[(L+I)^-1 (B x + y) - x],   B = I - V,
+ *     x     = x + alpha Delta,
+ * until ||Delta|| / ||B (L+I)^-1 y|| < tol, with (L+I)^-1 applied as an FFT,
+ * a pointwise multiply by 1/(Lhat+1) and an inverse FFT (Eq.
+ * laplacian_inverse).  All arithmetic of the iteration is FP32 on the GPU;
+ * norms are summed in FP64.
+ *
+ * Conventions for every entry point:
+ *   - Fields are C-contiguous, last axis fastest ([n0][n1][n2]); complex
+ *     fields are complex64 (two interleaved float32: re, im), 8-byte aligned
+ *     (16-byte aligned recommended).  A real potential is float32.
+ *   - "device pointer" = memory the GPU can address (cudaMalloc, torch CUDA
+ *     tensors); "host pointer" = ordinary (pinned or pageable) CPU memory.
+ *   - Every call returns a usp_status; no call aborts or throws.  On error
+ *     the outputs are unspecified unless stated; usp_last_error() gives a
+ *     one-line description of the last failure on the calling thread.
+ *   - Calls on one solver handle must not overlap in time (a handle is not
+ *     thread-safe); separate handles are independent.
+ */
+#ifndef USP_H
+#define USP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  USP_OK = 0,
+  USP_ERR_INVALID_ARG = 1,       /* null pointer, bad ndim, tol < 0, ...      */
+  USP_ERR_UNSUPPORTED_SIZE = 2,  /* an axis is not a power of two in [2,256]  */
+  USP_ERR_V_NOT_CONTRACTIVE = 3, /* max |V| >= 1 (Thm 1 needs ||V|| < 1)      */
+  USP_ERR_NOT_ACCRETIVE = 4,     /* Re(Lhat(p) + 1) <= 0 for some p (L+I not
+                                    invertible / A + B not accretive,
+                                    Corollary)                                */
+  USP_ERR_ALPHA_RANGE = 5,       /* alpha not finite or outside (0, 2]        */
+  USP_ERR_NOT_CONVERGED = 6,     /* maxit reached, or stagnation without
+                                    refinement; x holds the last iterate      */
+  USP_ERR_DIVERGED = 7,          /* ||Delta|| grew fourfold above its first
+                                    value: the contraction (Thm 1) does not
+                                    hold for these inputs                     */
+  USP_ERR_NONFINITE = 8,         /* NaN/Inf in V, y, x0 or an iterate         */
+  USP_ERR_CUDA = 9,              /* a CUDA runtime call failed                */
+  USP_ERR_OOM = 10               /* device allocation failed                  */
+} usp_status;
+
+/* Grid: ndim in {1,2,3}; n[0..ndim-1] axis lengths, n[ndim-1] fastest;
+ * each a power of two in [2, 256].  dx > 0 is the grid spacing (all axes). */
+typedef struct {
+  int32_t ndim;
+  int64_t n[3];
+  double dx;
+} usp_grid;
+
+/* Fourier symbol of L:  Lhat(p) = a |p|^2 + b  (complex a, b).
+ * Helmholtz (Sec. 3.1, Eq. laplacian_inverse): a = -1/c, b = kbar2/c.
+ * Diffusion (Sec. 3.2, scalar D, steady state): a = D/c, b = etabar/c. */
+typedef struct {
+  double a_re, a_im;
+  double b_re, b_im;
+} usp_lsymbol;
+
+/* Outcome of a solve (valid for USP_OK and USP_ERR_NOT_CONVERGED). */
+typedef struct {
+  int32_t iterations;        /* Delta evaluations, all phases together     */
+  int32_t converged;         /* 1 if the last ||Delta||/ref_norm < tol      */
+  int32_t refinements;       /* FP64 residual restarts performed            */
+  int32_t stagnated;         /* 1 if the FP32 iteration stopped improving  */
+  double final_rel_residual; /* last ||Delta|| / ref_norm                   */
+  double ref_norm;           /* ||B (L+I)^-1 y||, the alpha-free
+                                ||Gamma^-1 y|| of Algorithm 1's test        */
+  double alpha;              /* step size used                              */
+} usp_result;
+
+/* Solver options (usp_solver_set_options).  Zero-initialised = defaults. */
+typedef struct {
+  /* 0: refinement on (default) -- when the FP32 iteration reaches 8*tol or
+   *    stops improving, y - A x is formed in FP64 and the same FP32
+   *    iteration continues on the correction z with source y - A x, which
+   *    has exactly the same Delta (A + B = L + I, Sec. 2.1); x = x + z.
+   * 1: plain -- Algorithm 1 exactly: stop at tol or maxit.                 */
+  int32_t plain;
+  /* 0: automatic; 1: pencil schedule (one FFT axis per pass);
+   * 2: fused 3-D schedule (two passes per iteration; 3-D grids whose three
+   *    axes are all 256).                                                  */
+  int32_t schedule;
+  /* iterations per CUDA-graph launch between convergence polls; 0: auto   */
+  int32_t chunk;
+  /* maximum FP64 refinements per solve; 0: default (4)                     */
+  int32_t max_refinements;
+} usp_options;
+
+typedef struct usp_solver usp_solver;
+
+/* Create a solver for one operator A = L + V.
+ *   grid, lsym : see above (host pointers, copied).
+ *   V          : device pointer, N = prod(n) complex64 values, or float32
+ *                values if V_is_real != 0.  Copied into solver-owned device
+ *                memory before return; the caller may free it afterwards.
+ *   alpha      : step size; <= 0 selects alpha = Re[B^-1] = min_r Re
+ *                1/(1 - V(r)), the worst-case optimum of the
+ *                convergence-rate theorem (appendix).  alpha in (0, 1] is
+ *                always safe (Corollary).
+ *   cuda_stream: cudaStream_t the caller orders work on (0 = legacy
+ *                default stream).  Solves wait for work already queued on it.
+ * Validation (Sec. 2, Thm 1, Corollary): max |V| < 1, V finite,
+ * Re(Lhat(p) + 1) > 0 on the grid.  Allocates the solver's device memory
+ * (V copy, one scratch field, reduction buffers).  On success *out owns the
+ * solver; release it with usp_solver_destroy. */
+usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol* lsym,
+                             const void* V, int32_t V_is_real, double alpha,
+                             void* cuda_stream, usp_solver** out);
+
+/* Replace the options of a solver (host pointer, copied). */
+usp_status usp_solver_set_options(usp_solver* s, const usp_options* opt);
+
+/* Algorithm 1 (Sec. 2.1).
+ *   y       : device pointer, N complex64, the canonical source (borrowed
+ *             for the duration of the call, not modified).
+ *   x       : device pointer, N complex64.  In: the initial estimate if
+ *             use_x0 != 0 (otherwise ignored, the iteration starts at 0).
+ *             Out: the last iterate.
+ *   tol     : stop when ||Delta_i|| / ref_norm < tol (tol >= 0; 0 runs
+ *             exactly maxit iterations in plain mode).
+ *   maxit   : iteration limit (>= 1), counted over all refinement phases.
+ *   ref_norm: > 0 uses this denominator (e.g. to resume a solve); <= 0
+ *             computes ||B (L+I)^-1 y|| (one extra FFT pair if use_x0).
+ * Returns USP_OK when converged, USP_ERR_NOT_CONVERGED when maxit is hit
+ * or the plain FP32 iteration stagnates (x and *out still valid),
+ * USP_ERR_NONFINITE / USP_ERR_DIVERGED on failure.  Synchronous: returns
+ * after the GPU work finished.  *out may be NULL. */
+usp_status usp_solve(usp_solver* s, const void* y, void* x, int32_t use_x0,
+                     double tol, int32_t maxit, double ref_norm,
+                     usp_result* out);
+
+/* The same solve with host buffers: y_host (N complex64) is copied to the
+ * device, the solve runs on solver-owned device buffers, and the result is
+ * copied back into x_host (which also supplies x0 when use_x0 != 0).
+ * Pinned host memory gives the fastest copies. */
+usp_status usp_solve_host(usp_solver* s, const void* y_host, void* x_host,
+                          int32_t use_x0, double tol, int32_t maxit,
+                          double ref_norm, usp_result* out);
+
+/* Residual history of the last solve: history[i] = ||Delta_{i+1}||/ref_norm
+ * (Fig. 1d plots this quantity).  Copies min(capacity, count) values into
+ * host_out (host pointer) and writes the count to *n_out. */
+usp_status usp_residual_history(const usp_solver* s, double* host_out,
+                                int32_t capacity, int32_t* n_out);
+
+/* Forward operator A x = L x + V x (Sec. 2, the problem statement), in FP64
+ * arithmetic on the GPU, for the unpreconditioned residual ||A x - y||/||y||
+ * of the paper's tables (Sec. 4.1).  x, Ax: device pointers, N complex64;
+ * Ax may not alias x. */
+usp_status usp_apply_A(usp_solver* s, const void* x, void* Ax);
+
+/* r = y - A x in FP64 arithmetic (the refinement residual); r is written as
+ * complex64 (device pointer) and, if rel_out is not NULL, ||r||/||y|| (FP64)
+ * to *rel_out (host pointer).  r may be NULL when only the norm is wanted. */
+usp_status usp_residual(usp_solver* s, const void* x, const void* y, void* r,
+                        double* rel_out);
+
+/* The step size the solver uses (host pointer out). */
+usp_status usp_solver_alpha(const usp_solver* s, double* alpha_out);
+
+/* Free all resources of a solver (NULL is ignored). */
+void usp_solver_destroy(usp_solver* s);
+
+/* Canonical form on the host, FP64 (Sec. 2.2 and 3.1).  Helmholtz problem
+ * laplacian(psi) + k2(r) psi = -S(r):
+ *   kbar2, rho = centre and radius of the smallest circle enclosing the
+ *   values k2(r) (the smallest-circle problem; Welzl's algorithm);
+ *   c = -rho/(0.95 i) scaled by norm_v: c = i rho / norm_v;
+ *   V = (k2 - kbar2)/c, y = -S/c, a = -1/c, b = kbar2/c.
+ * k2, S: host pointers to n complex128 values (interleaved doubles).
+ * V_out, y_out: host pointers to n complex64 values (written).
+ * lsym_out, c_out (2 doubles: re, im), bias_out (2 doubles): written.
+ * norm_v in (0, 1) (the paper uses 0.95).  Returns USP_ERR_INVALID_ARG for
+ * a homogeneous medium (rho = 0: c undefined). */
+usp_status usp_canon_helmholtz(const double* k2, const double* S, int64_t n,
+                               double norm_v, float* V_out, float* y_out,
+                               usp_lsymbol* lsym_out, double* c_out,
+                               double* bias_out);
+
+/* Canonical form of steady diffusion -D laplacian(u) + eta(r) u = S(r)
+ * (Sec. 3.2 with scalar constant D): etabar, rho = midpoint and half-range
+ * of eta; c = rho / norm_v (real, positive); V = (eta - etabar)/c (real),
+ * y = S/c, a = D/c, b = etabar/c.
+ * eta: host, n doubles.  S: host, n complex128.  V_out: host, n float32.
+ * y_out: host, n complex64.  c_out: 1 double. */
+usp_status usp_canon_diffusion(const double* eta, double D, const double* S,
+                               int64_t n, double norm_v, float* V_out,
+                               float* y_out, usp_lsymbol* lsym_out,
+                               double* c_out, double* bias_out);
+
+/* ---- measurement (no counterpart in the paper; used by the benchmark) -- */
+
+/* Mean duration of each kernel of one iteration. */
+typedef struct {
+  char name[32];      /* pass name, e.g. "rows_inv_post"                     */
+  int32_t launches;   /* launches timed                                      */
+  double ms;          /* mean duration per launch, CUDA events on the
+                         solver's stream, milliseconds                        */
+  double bytes;       /* algorithmic HBM bytes one launch moves (each input
+                         read once, each output written once)                 */
+} usp_pass_time;
+
+/* Run `iters` iterations of the solver's schedule on (y, x) -- device
+ * pointers as in usp_solve; x is overwritten -- launching every kernel
+ * directly with a CUDA event before and after it, and report per-kernel
+ * mean durations.  out: host array of `capacity` entries; *n_out = number
+ * of kernels per iteration. */
+usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int32_t iters,
+                           usp_pass_time* out, int32_t capacity, int32_t* n_out);
+
+/* Number of kernel launches this library has issued in this process (a
+ * CUDA-graph launch counts each kernel node it runs). */
+int64_t usp_kernel_launches(void);
+
+/* Human-readable name of a status code (static string). */
+const char* usp_status_string(usp_status st);
+
+/* Description of the last error on the calling thread (static storage,
+ * valid until the next failing call on this thread). */
+const char* usp_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t usp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* USP_H */

@@ -1,0 +1,178 @@
+// fft_core.cuh -- building blocks of the FFT that applies (L+I)^-1 =
+// F^-1 diag(1/(Lhat+1)) F (paper Eq. laplacian_inverse).
+//
+// A length-N transform (N = 2^k, 2 <= N <= 256) is split as N = N1 * N2 with
+// N2 <= N1 <= 16 (N1 = 2^ceil(k/2)):
+//   n = N2*n1 + n2,  k = k1 + N1*k2,
+//   X[k1 + N1 k2] = sum_n2 W_N^(n2 k1) W_N2^(n2 k2) sum_n1 x[N2 n1 + n2] W_N1^(n1 k1)
+// G = N2 cooperating threads each hold N1 values.  Stage 1: thread g holds
+// x[N2 q + g] (q = 0..N1-1), does an in-register DFT_N1 and multiplies by the
+// twiddle W_N^(g k1).  One exchange through shared memory.  Stage 2: thread g
+// does S = N1/N2 in-register DFT_N2's for k1 = g + G s and ends up holding
+// X[g + G s + N1 k2] in register s*N2 + k2.  That set of indices is the set
+// {g + G m}, the same set the thread held on input, so a forward transform,
+// a pointwise spectral multiply and an inverse transform chain in registers
+// with one compile-time register permutation (m = s + S k2).
+//
+// Forward transforms are unnormalised with W_N = exp(-2 pi i / N); inverse
+// transforms use the conjugate twiddles and no 1/N (the caller folds 1/N
+// into the spectral multiplier).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace usp {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { typedef float2 type; };
+template <> struct cplx_of<double> { typedef double2 type; };
+
+template <typename V>
+__device__ __forceinline__ V mkc(decltype(V().x) re, decltype(V().x) im) {
+  V r; r.x = re; r.y = im; return r;
+}
+template <typename V>
+__device__ __forceinline__ V cadd(V a, V b) { return mkc<V>(a.x + b.x, a.y + b.y); }
+template <typename V>
+__device__ __forceinline__ V csub(V a, V b) { return mkc<V>(a.x - b.x, a.y - b.y); }
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+  return mkc<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V>
+__device__ __forceinline__ V cmulc(V a, V b) {
+  return mkc<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// a * (-i) for the forward direction, a * (+i) for the inverse.
+template <bool INV, typename V>
+__device__ __forceinline__ V rot_quarter(V a) {
+  return INV ? mkc<V>(-a.y, a.x) : mkc<V>(a.y, -a.x);
+}
+
+// cos(pi/8), sin(pi/8), sqrt(1/2): the non-trivial values of exp(2 pi i e/16).
+#define USP_COS_PI_8 0.92387953251128675613
+#define USP_SIN_PI_8 0.38268343236508977173
+#define USP_SQRT_HALF 0.70710678118654752440
+
+// a * W_16^e (forward: W_16 = exp(-2 pi i/16); inverse: its conjugate).
+// e is a compile-time constant after unrolling, so the switch folds away.
+template <bool INV, typename V>
+__device__ __forceinline__ V tw16(V a, int e) {
+  typedef decltype(a.x) T;
+  e &= 15;
+  const int q = e >> 2, r = e & 3;
+  V b = a;
+  if (r == 2) {
+    // exp(-+ i pi/4) = sqrt(1/2) (1 -+ i)
+    const T h = T(USP_SQRT_HALF);
+    b = INV ? mkc<V>(h * (a.x - a.y), h * (a.x + a.y))
+            : mkc<V>(h * (a.x + a.y), h * (a.y - a.x));
+  } else if (r == 1 || r == 3) {
+    const T c = T(r == 1 ? USP_COS_PI_8 : USP_SIN_PI_8);
+    const T s = T(r == 1 ? USP_SIN_PI_8 : USP_COS_PI_8);
+    // forward W = c - i s ; inverse W = c + i s
+    b = INV ? mkc<V>(a.x * c - a.y * s, a.x * s + a.y * c)
+            : mkc<V>(a.x * c + a.y * s, a.y * c - a.x * s);
+  }
+  if (q & 2) b = mkc<V>(-b.x, -b.y);
+  if (q & 1) b = rot_quarter<INV>(b);
+  return b;
+}
+
+// In-register DFT of size R in {1,2,4,8,16}, natural order in and out
+// (radix-2 decimation in time, fully unrolled).
+template <int R, bool INV, typename V>
+struct DFT {
+  static __device__ __forceinline__ void run(V* v) {
+    constexpr int H = R / 2;
+    V e[H], o[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    DFT<H, INV, V>::run(e);
+    DFT<H, INV, V>::run(o);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      V t = tw16<INV>(o[k], k * (16 / R));
+      v[k] = cadd(e[k], t);
+      v[k + H] = csub(e[k], t);
+    }
+  }
+};
+template <bool INV, typename V>
+struct DFT<1, INV, V> {
+  static __device__ __forceinline__ void run(V*) {}
+};
+template <bool INV, typename V>
+struct DFT<2, INV, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    V t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  }
+};
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+template <int N>
+struct Split {
+  static constexpr int LOG = ilog2c(N);
+  static constexpr int N1 = 1 << ((LOG + 1) / 2);
+  static constexpr int N2 = N / N1;
+  static constexpr int G = N2;        // threads per transform
+  static constexpr int S = N1 / N2;   // stage-2 sub-transforms per thread (1 or 2)
+  static_assert(N1 * N2 == N && N2 <= N1 && N1 <= 16, "unsupported FFT size");
+};
+
+// Stage 1: in-register DFT_N1, then v[k1] *= W_N^(g k1) (conjugate if INV).
+// tw[m] = W_N^m, m in [0, N).
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void stage1(V* v, int g, const V* tw) {
+  constexpr int N1 = Split<N>::N1;
+  DFT<N1, INV, V>::run(v);
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) {
+    const V w = tw[g * k1];
+    v[k1] = INV ? cmulc(v[k1], w) : cmul(v[k1], w);
+  }
+}
+
+// Stage 2 on values already gathered: w[s*N2 + n2] = A[k1 = g + G s][n2];
+// out in place: w[s*N2 + k2] = X[g + G s + N1 k2].
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void stage2(V* w) {
+  constexpr int N2 = Split<N>::N2, S = Split<N>::S;
+#pragma unroll
+  for (int s = 0; s < S; ++s) DFT<N2, INV, V>::run(w + s * N2);
+}
+
+// Index held in output register q (= s*N2 + k2) by thread g.
+template <int N>
+__device__ __forceinline__ int out_index(int g, int q) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G;
+  return g + G * (q / N2) + N1 * (q % N2);
+}
+// Index held in input register q by thread g (stage-1 distribution).
+template <int N>
+__device__ __forceinline__ int in_index(int g, int q) {
+  return Split<N>::N2 * q + g;
+}
+// Reorder output registers into the stage-1 input distribution, so that a
+// second transform can start from them: in[s + S k2] = out[s N2 + k2].
+template <int N, typename V>
+__device__ __forceinline__ void out_to_in(const V* o, V* i) {
+  constexpr int N2 = Split<N>::N2, S = Split<N>::S;
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) i[s + S * k2] = o[s * N2 + k2];
+}
+
+// Frequency index k in [0,n) to signed FFT-order m in [-n/2, n/2).
+__device__ __forceinline__ int signed_freq(int k, int n) { return k < (n >> 1) ? k : k - n; }
+
+}  // namespace usp

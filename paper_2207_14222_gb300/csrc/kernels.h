@@ -1,0 +1,138 @@
+// kernels.h -- internal interface between the solver runtime (usp_api.cpp)
+// and the CUDA kernels.  Not part of the public ABI (include/usp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace usp {
+
+// Device-side iteration state: one per solver.  Written by the last block
+// of the kernel that finishes an iteration (the update pass), read by every
+// kernel at entry (done != 0: skip all work) and by the host between CUDA
+// graph launches.
+enum DevStatus : int {
+  ST_RUNNING = 0,
+  ST_CONVERGED = 1,   // ||Delta||/ref < tol
+  ST_MAXIT = 2,       // it reached it_limit
+  ST_NONFINITE = 3,   // NaN/Inf norm
+  ST_DIVERGED = 4,    // ||Delta|| above 4x its first value in this phase
+  ST_STAGNATED = 5    // no 0.1% improvement over stall_window iterations
+};
+
+struct DevState {
+  int done;           // nonzero: every kernel returns at entry
+  int status;         // DevStatus
+  int it;             // Delta evaluations completed (all phases)
+  int it_limit;       // stop at this count (status ST_MAXIT)
+  int phase_start;    // value of `it` when the current phase began
+  int best_it;        // iteration of best_r
+  int stall_window;   // 0 disables the stagnation test
+  unsigned int ticket;  // last-block-done counter of the update pass
+  double tol;         // stop when r < tol
+  double ref;         // ||Delta_ref||; <= 0: taken from the next Delta (x0 = 0)
+  double last_r;      // last ||Delta||/ref
+  double best_r;
+  double phase_first_r;
+  double sumsq;       // last ||Delta||^2 (FP64)
+};
+
+// Kernel flags.
+enum : int {
+  F_XZERO = 1,      // the iterate is zero: do not read x
+  F_REF = 2,        // reference pass: Delta at x = 0, store ||Delta|| in ref, no update
+  F_NOSTATE = 4,    // ignore the device state (stand-alone transforms)
+  F_APPLY_A = 8,    // residual pass writes A x instead of y - A x
+  F_VREAL = 16      // V is float32 (real potential)
+};
+
+// Rows pass (transform along the contiguous last axis): a bit set of
+// input, transform and output stages.
+enum RowMode : int {
+  R_IN_PRE = 1,      // t = (1-V) x + y from complex64 x, y        (fp32 only)
+  R_IN_X = 2,        // t = x (complex64, upcast)                   (fp64 only)
+  R_IN_BUF = 4,      // t = scratch row
+  R_FWD = 8,         // forward transform
+  R_MUL = 16,        // multiply by the spectral factor (needs R_FWD)
+  R_INV = 32,        // inverse transform
+  R_OUT_BUF = 64,    // scratch row = result
+  R_OUT_POST = 128,  // Delta = (1-V)(u - x); x += alpha Delta; ||Delta||^2 (fp32)
+  R_OUT_RESID = 256  // r = y - (u + V x)  [or A x = u + V x]; norms  (fp64)
+};
+
+// Strided-axis pass modes.
+enum ColMode : int {
+  COL_FWD = 0,
+  COL_INV = 1,
+  COL_FWD_MUL_INV = 2   // transform, multiply by the spectral factor, inverse
+};
+
+enum MulKind : int {
+  MUL_LINV = 0,   // 1 / (N (Lhat(p) + 1))
+  MUL_L = 1       // Lhat(p) / N
+};
+
+// Spectral symbol Lhat(p) = a |p|^2 + b on the grid; p_ax = ks[ax] * m_ax.
+template <typename T>
+struct Sym {
+  T a_re, a_im, b_re, b_im;
+  T inv_n;        // 1 / (total number of points)
+  T ks[3];        // 2 pi / (n_ax dx) per axis (axis 0 slowest)
+  int n[3];
+  int ndim;
+};
+
+template <typename T>
+struct RowsArgs {
+  int mode;             // RowMode bit set
+  int mul;              // MulKind for R_MUL
+  int flags;
+  int64_t nrows;        // number of rows (length-N lines along the last axis)
+  const float2* x_in;   // complex64 iterate (or correction z)
+  float2* x_out;        // complex64 iterate out (may alias x_in)
+  const float2* y;      // complex64 source
+  const void* V;        // complex64, or float32 with F_VREAL
+  void* buf;            // complex scratch of type cplx_of<T>
+  float2* r_out;        // ROW_INV_RESID output (complex64)
+  double* partials;     // one (or two) doubles per block
+  DevState* st;
+  double* hist;
+  T alpha;
+  Sym<T> sym;
+};
+
+template <typename T>
+struct ColsArgs {
+  int mode;
+  int mul;              // MulKind for COL_FWD_MUL_INV
+  int flags;
+  int64_t inner;        // S: stride of the axis = number of columns per outer slab
+  int64_t outer;        // number of outer slabs
+  int64_t inner_blocks; // ceil(inner / 32)
+  void* buf;            // complex scratch of type cplx_of<T>, in place
+  DevState* st;
+  Sym<T> sym;
+};
+
+// Launchers (pencil_kernels.cu).  n = transform length (power of two, 2..256).
+cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaStream_t s);
+cudaError_t launch_rows_f64(int n, const RowsArgs<double>& a, int64_t grid, cudaStream_t s);
+cudaError_t launch_cols_f32(int n, const ColsArgs<float>& a, cudaStream_t s);
+cudaError_t launch_cols_f64(int n, const ColsArgs<double>& a, cudaStream_t s);
+int rows_per_block_f32(int n);
+int rows_per_block_f64(int n);
+
+// Auxiliary kernels (pencil_kernels.cu).
+cudaError_t init_twiddles();
+// Per-block statistics of V (max |V|, min Re 1/(1-V), nonfinite count) then
+// their reduction into out[3] (device).
+cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials,
+                           int nblocks, double* out, cudaStream_t s);
+// x += z (complex64).
+cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s);
+// Sum `count` partial pairs (2 doubles per block) into out[2].
+cudaError_t launch_sum_pairs(const double* partials, int count, double* out, cudaStream_t s);
+// Copy a real float32 or complex64 potential into solver storage.
+cudaError_t launch_copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
+}  // namespace usp

@@ -1,0 +1,632 @@
+// pencil_kernels.cu -- the pencil schedule of one fixed-point iteration
+// (paper Algorithm 1 on the forward-eliminated operator of Sec. 2.1):
+//
+//   rows pass   : t = (1-V) x + y ; FFT along the contiguous axis      [B x + y]
+//   column pass : FFT along each strided axis; on the outermost axis
+//                 FFT -> multiply by 1/(N (Lhat(p)+1)) -> inverse FFT   [(L+I)^-1,
+//                                                                        Eq. laplacian_inverse]
+//   column pass : inverse FFT along the remaining strided axes
+//   rows pass   : inverse FFT along the contiguous axis;
+//                 Delta = (1-V)(u - x); x += alpha Delta; ||Delta||^2   [Delta, update,
+//                                                                        convergence test]
+//
+// The same kernels, instantiated in FP64 with the multiplier Lhat(p)/N, form
+// the residual y - A x used by iterative refinement.
+//
+// Memory layout: C order, last axis fastest.  Rows kernels: G = N2 adjacent
+// lanes own one row, each thread holds N1 values (see fft_core.cuh), so for
+// a fixed register the G threads touch G consecutive elements.  Column
+// kernels: one warp per stage-1 thread index g, the 32 lanes own 32
+// consecutive columns, so every global access of a warp is 32 consecutive
+// complex values.
+#include <math.h>
+
+#include "fft_core.cuh"
+#include "kernels.h"
+
+namespace usp {
+
+// W_256^m = exp(-2 pi i m/256), m in [0,256).  W_n^m = W_256^(m 256/n).
+__device__ float2 g_tw32[256];
+__device__ double2 g_tw64[256];
+
+template <typename T>
+__device__ __forceinline__ typename cplx_of<T>::type tw_entry(int m);
+template <>
+__device__ __forceinline__ float2 tw_entry<float>(int m) { return g_tw32[m]; }
+template <>
+__device__ __forceinline__ double2 tw_entry<double>(int m) { return g_tw64[m]; }
+
+template <typename T> struct RowsCfg;
+template <> struct RowsCfg<float> { static constexpr int THREADS = 256; };
+template <> struct RowsCfg<double> { static constexpr int THREADS = 128; };
+
+// ------------------------------------------------------------ reductions ---
+
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < THREADS / 32; ++i) s += red[i];
+  }
+  return s;  // valid in thread 0
+}
+
+// Iteration bookkeeping after ||Delta||^2 is known (Algorithm 1's test).
+__device__ void finalize_iteration(DevState* st, double* hist, double sumsq, int flags) {
+  const double nrm = sqrt(sumsq);
+  if (flags & F_REF) {
+    st->ref = nrm;
+    if (!isfinite(nrm)) {
+      st->status = ST_NONFINITE;
+      st->done = 1;
+    }
+    return;
+  }
+  if (st->it >= st->it_limit) {  // never write past the history buffer
+    st->status = ST_MAXIT;
+    st->done = 1;
+    return;
+  }
+  st->sumsq = sumsq;
+  if (!isfinite(nrm)) {
+    st->last_r = nrm;
+    st->status = ST_NONFINITE;
+    st->done = 1;
+    return;
+  }
+  double ref = st->ref;
+  if (ref <= 0.0) {  // x0 = 0: Delta_1 = B (L+I)^-1 y, the reference itself
+    ref = nrm;
+    st->ref = nrm;
+  }
+  const double r = ref > 0.0 ? nrm / ref : 0.0;
+  const int it = st->it;
+  hist[it] = r;
+  st->it = it + 1;
+  st->last_r = r;
+  if (it == st->phase_start) {
+    st->phase_first_r = r;
+    st->best_r = r;
+    st->best_it = it + 1;
+  }
+  if (r < st->tol || ref == 0.0) {
+    st->status = ST_CONVERGED;
+    st->done = 1;
+    return;
+  }
+  if (it > st->phase_start && r > 4.0 * st->phase_first_r) {
+    st->status = ST_DIVERGED;
+    st->done = 1;
+    return;
+  }
+  if (it + 1 >= st->it_limit) {
+    st->status = ST_MAXIT;
+    st->done = 1;
+    return;
+  }
+  if (st->stall_window > 0) {
+    if (r < st->best_r * (1.0 - 1e-3)) {
+      st->best_r = r;
+      st->best_it = it + 1;
+    } else if (it + 1 - st->best_it >= st->stall_window) {
+      st->status = ST_STAGNATED;
+      st->done = 1;
+    }
+  }
+}
+
+// Block partial of ||Delta||^2, then the last block to finish sums all
+// partials in a fixed order (deterministic) and updates the state.
+template <int THREADS>
+__device__ void reduce_and_finalize(double acc, double* partials, DevState* st, double* hist,
+                                    int flags) {
+  __shared__ double red[THREADS / 32];
+  __shared__ int is_last;
+  const double bs = block_sum<THREADS>(acc, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned t = atomicAdd(&st->ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += THREADS) s += __ldcg(partials + i);
+  const double tot = block_sum<THREADS>(s, red);
+  if (threadIdx.x == 0) {
+    finalize_iteration(st, hist, tot, flags);
+    st->ticket = 0u;
+  }
+}
+
+// ------------------------------------------------------- spectral factor ---
+
+template <typename T, typename V>
+__device__ __forceinline__ V spectral_factor(T p2, const Sym<T>& s, int mul) {
+  const T lr = s.a_re * p2 + s.b_re;
+  const T li = s.a_im * p2 + s.b_im;
+  if (mul == MUL_L) return mkc<V>(lr * s.inv_n, li * s.inv_n);
+  const T dr = lr + T(1);
+  const T sc = s.inv_n / (dr * dr + li * li);
+  return mkc<V>(dr * sc, -li * sc);
+}
+
+// |p|^2 contributed by axis `ax` at frequency index k.
+template <typename T>
+__device__ __forceinline__ T axis_p2(const Sym<T>& s, int ax, int k) {
+  const T p = s.ks[ax] * T(signed_freq(k, s.n[ax]));
+  return p * p;
+}
+
+// --------------------------------------------------------------- rows ---
+
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void fft_rows(V* v, V* exr, const V* tw, int g) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
+  stage1<N, INV>(v, g, tw);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) exr[k1 * N2 + (g ^ (k1 & (N2 - 1)))] = v[k1];
+  __syncthreads();
+  V w[N1];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int k1 = g + G * s;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = exr[k1 * N2 + (n2 ^ (k1 & (N2 - 1)))];
+  }
+  __syncthreads();
+  stage2<N, INV>(w);
+#pragma unroll
+  for (int q = 0; q < N1; ++q) v[q] = w[q];
+}
+
+__device__ __forceinline__ float2 load_v(const void* V, int64_t i, bool vreal) {
+  if (vreal) return make_float2(__ldg(reinterpret_cast<const float*>(V) + i), 0.f);
+  return __ldg(reinterpret_cast<const float2*>(V) + i);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(RowsCfg<T>::THREADS) k_rows(const RowsArgs<T> a) {
+  typedef typename cplx_of<T>::type V;
+  constexpr int N1 = Split<N>::N1, G = Split<N>::G;
+  constexpr int THREADS = RowsCfg<T>::THREADS;
+  constexpr int F = THREADS / G;  // rows per block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tw = reinterpret_cast<V*>(smem_raw);
+  V* ex = tw + N;
+
+  if (!(a.flags & F_NOSTATE) && a.st->done) return;
+
+  const int tid = threadIdx.x, f = tid / G, g = tid % G;
+  const int64_t row = (int64_t)blockIdx.x * F + f;
+  const bool active = row < a.nrows;
+  const int64_t base = row * N;
+  const bool xzero = (a.flags & F_XZERO) != 0;
+  const bool vreal = (a.flags & F_VREAL) != 0;
+  for (int m = tid; m < N; m += THREADS) tw[m] = tw_entry<T>(m * (256 / N));
+  __syncthreads();
+  V* exr = ex + f * N;
+
+  V v[N1];
+  // ---- input stage (stage-1 distribution: register q holds index N2 q + g)
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    const int64_t i = base + in_index<N>(g, q);
+    V t = mkc<V>(T(0), T(0));
+    if (active) {
+      if (a.mode & R_IN_BUF) {
+        t = reinterpret_cast<const V*>(a.buf)[i];
+      } else if (a.mode & R_IN_X) {
+        const float2 xv = a.x_in[i];
+        t = mkc<V>(T(xv.x), T(xv.y));
+      } else {  // R_IN_PRE: B x + y
+        const float2 yv = a.y[i];
+        float2 tv = yv;
+        if (!xzero) {
+          const float2 vv = load_v(a.V, i, vreal);
+          const float2 xv = a.x_in[i];
+          const float br = 1.f - vv.x, bi = -vv.y;
+          tv.x += br * xv.x - bi * xv.y;
+          tv.y += br * xv.y + bi * xv.x;
+        }
+        t = mkc<V>(T(tv.x), T(tv.y));
+      }
+    }
+    v[q] = t;
+  }
+  // ---- transforms
+  if (a.mode & R_FWD) fft_rows<N, false>(v, exr, tw, g);
+  if (a.mode & R_MUL) {
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int k = out_index<N>(g, q);
+      v[q] = cmul(v[q], spectral_factor<T, V>(axis_p2(a.sym, 0, k), a.sym, a.mul));
+    }
+  }
+  if (a.mode & R_INV) {
+    if (a.mode & R_FWD) {
+      V t[N1];
+      out_to_in<N>(v, t);
+#pragma unroll
+      for (int q = 0; q < N1; ++q) v[q] = t[q];
+    }
+    fft_rows<N, true>(v, exr, tw, g);
+  }
+  // ---- output stage (register q holds index out_index(g, q))
+  if (a.mode & R_OUT_BUF) {
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < N1; ++q)
+        reinterpret_cast<V*>(a.buf)[base + out_index<N>(g, q)] = v[q];
+    }
+    return;
+  }
+  if (a.mode & R_OUT_POST) {
+    // Delta = (1-V)(u - x) ; x += alpha Delta  (Algorithm 1)
+    float acc = 0.f;
+    if (active) {
+      const float al = float(a.alpha);
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        const int64_t i = base + out_index<N>(g, q);
+        const float2 vv = load_v(a.V, i, vreal);
+        const float2 xv = xzero ? make_float2(0.f, 0.f) : a.x_in[i];
+        const float ur = float(v[q].x) - xv.x, ui = float(v[q].y) - xv.y;
+        const float br = 1.f - vv.x, bi = -vv.y;
+        const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
+        acc += dr * dr + di * di;
+        if (!(a.flags & F_REF)) a.x_out[i] = make_float2(xv.x + al * dr, xv.y + al * di);
+      }
+    }
+    reduce_and_finalize<THREADS>((double)acc, a.partials, a.st, a.hist, a.flags);
+    return;
+  }
+  if (a.mode & R_OUT_RESID) {
+    // u = L x ; A x = u + V x ; r = y - A x  (fp64)
+    double acc_r = 0.0, acc_y = 0.0;
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        const int64_t i = base + out_index<N>(g, q);
+        const float2 vv = load_v(a.V, i, vreal);
+        const float2 xv = a.x_in[i];
+        const double ax = double(v[q].x) + (double(vv.x) * xv.x - double(vv.y) * xv.y);
+        const double ay = double(v[q].y) + (double(vv.x) * xv.y + double(vv.y) * xv.x);
+        double rx = ax, ry = ay;
+        if (!(a.flags & F_APPLY_A)) {
+          const float2 yv = a.y[i];
+          rx = double(yv.x) - ax;
+          ry = double(yv.y) - ay;
+          acc_y += double(yv.x) * yv.x + double(yv.y) * yv.y;
+        }
+        acc_r += rx * rx + ry * ry;
+        if (a.r_out) a.r_out[i] = make_float2(float(rx), float(ry));
+      }
+    }
+    __shared__ double red[THREADS / 32];
+    const double sr = block_sum<THREADS>(acc_r, red);
+    const double sy = block_sum<THREADS>(acc_y, red);
+    if (threadIdx.x == 0) {
+      a.partials[2 * blockIdx.x] = sr;
+      a.partials[2 * blockIdx.x + 1] = sy;
+    }
+  }
+}
+
+// ------------------------------------------------------------ columns ---
+
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void fft_cols(V* v, V* ex, const V* tw, int g, int lane) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
+  stage1<N, INV>(v, g, tw);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * 32 + lane] = v[k1];
+  __syncthreads();
+  V w[N1];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int k1 = g + G * s;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * 32 + lane];
+  }
+  __syncthreads();
+  stage2<N, INV>(w);
+#pragma unroll
+  for (int q = 0; q < N1; ++q) v[q] = w[q];
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) {
+  typedef typename cplx_of<T>::type V;
+  constexpr int N1 = Split<N>::N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tw = reinterpret_cast<V*>(smem_raw);
+  V* ex = tw + N;
+
+  if (!(a.flags & F_NOSTATE) && a.st->done) return;
+
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t ib = blockIdx.x % a.inner_blocks, o = blockIdx.x / a.inner_blocks;
+  const int64_t col = ib * 32 + lane;
+  const bool active = col < a.inner;
+  const int64_t base = o * (int64_t)N * a.inner + col;
+  V* buf = reinterpret_cast<V*>(a.buf);
+  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = tw_entry<T>(m * (256 / N));
+  __syncthreads();
+
+  V v[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q)
+    v[q] = active ? buf[base + (int64_t)in_index<N>(g, q) * a.inner] : mkc<V>(T(0), T(0));
+
+  if (a.mode == COL_INV) {
+    fft_cols<N, true>(v, ex, tw, g, lane);
+  } else {
+    fft_cols<N, false>(v, ex, tw, g, lane);
+    if (a.mode == COL_FWD_MUL_INV) {
+      // This pass runs on axis 0 after all faster axes were transformed, so
+      // the column index decomposes into their frequency indices.
+      T p2in = T(0);
+      if (a.sym.ndim == 3) {
+        p2in = axis_p2(a.sym, 2, int(col % a.sym.n[2])) + axis_p2(a.sym, 1, int(col / a.sym.n[2]));
+      } else if (a.sym.ndim == 2) {
+        p2in = axis_p2(a.sym, 1, int(col));
+      }
+      V t[N1];
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        const int k = out_index<N>(g, q);
+        v[q] = cmul(v[q], spectral_factor<T, V>(p2in + axis_p2(a.sym, 0, k), a.sym, a.mul));
+      }
+      out_to_in<N>(v, t);
+#pragma unroll
+      for (int q = 0; q < N1; ++q) v[q] = t[q];
+      fft_cols<N, true>(v, ex, tw, g, lane);
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < N1; ++q) buf[base + (int64_t)out_index<N>(g, q) * a.inner] = v[q];
+  }
+}
+
+// ------------------------------------------------------------ launchers ---
+
+template <typename T, int N>
+static size_t rows_smem() {
+  typedef typename cplx_of<T>::type V;
+  return sizeof(V) * (N + (RowsCfg<T>::THREADS / Split<N>::G) * N);
+}
+template <typename T, int N>
+static size_t cols_smem() {
+  typedef typename cplx_of<T>::type V;
+  return sizeof(V) * (N + 32 * N);
+}
+
+template <typename T, int N>
+static cudaError_t rows_attr() {
+  return cudaFuncSetAttribute(k_rows<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rows_smem<T, N>());
+}
+template <typename T, int N>
+static cudaError_t cols_attr() {
+  return cudaFuncSetAttribute(k_cols<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)cols_smem<T, N>());
+}
+
+template <typename T, int N>
+static cudaError_t rows_go(const RowsArgs<T>& a, int64_t grid, cudaStream_t s) {
+  k_rows<T, N><<<(unsigned)grid, RowsCfg<T>::THREADS, rows_smem<T, N>(), s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int N>
+static cudaError_t cols_go(const ColsArgs<T>& a, cudaStream_t s) {
+  const int64_t grid = a.inner_blocks * a.outer;
+  k_cols<T, N><<<(unsigned)grid, 32 * Split<N>::G, cols_smem<T, N>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+#define USP_SWITCH_N(n, CALL)                     \
+  switch (n) {                                    \
+    case 2: return CALL(2);                       \
+    case 4: return CALL(4);                       \
+    case 8: return CALL(8);                       \
+    case 16: return CALL(16);                     \
+    case 32: return CALL(32);                     \
+    case 64: return CALL(64);                     \
+    case 128: return CALL(128);                   \
+    case 256: return CALL(256);                   \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaStream_t s) {
+#define C_(N) rows_go<float, N>(a, grid, s)
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+cudaError_t launch_rows_f64(int n, const RowsArgs<double>& a, int64_t grid, cudaStream_t s) {
+#define C_(N) rows_go<double, N>(a, grid, s)
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+cudaError_t launch_cols_f32(int n, const ColsArgs<float>& a, cudaStream_t s) {
+#define C_(N) cols_go<float, N>(a, s)
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+cudaError_t launch_cols_f64(int n, const ColsArgs<double>& a, cudaStream_t s) {
+#define C_(N) cols_go<double, N>(a, s)
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+
+int rows_per_block_f32(int n) { return RowsCfg<float>::THREADS / (n / (1 << ((ilog2c(n) + 1) / 2))); }
+int rows_per_block_f64(int n) { return RowsCfg<double>::THREADS / (n / (1 << ((ilog2c(n) + 1) / 2))); }
+
+template <typename T, int N>
+static cudaError_t attrs_one() {
+  cudaError_t e = rows_attr<T, N>();
+  if (e != cudaSuccess) return e;
+  return cols_attr<T, N>();
+}
+template <typename T>
+static cudaError_t attrs_all() {
+  cudaError_t e;
+  if ((e = attrs_one<T, 2>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 4>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 8>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 16>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 32>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 64>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 128>()) != cudaSuccess) return e;
+  return attrs_one<T, 256>();
+}
+
+// Twiddles from the first octant by symmetry, so W^(64 j) are exactly
+// 1, -i, -1, i and the table is exactly symmetric.
+cudaError_t init_twiddles() {
+  float2 h32[256];
+  double2 h64[256];
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < 256; ++m) {
+    const int q = m / 64, r = m % 64;
+    double c, s;  // cos, sin of 2 pi r/256, r in [0, 64)
+    if (r <= 32) {
+      c = cos(two_pi * r / 256.0);
+      s = sin(two_pi * r / 256.0);
+    } else {
+      c = sin(two_pi * (64 - r) / 256.0);
+      s = cos(two_pi * (64 - r) / 256.0);
+    }
+    if (r == 0) { c = 1.0; s = 0.0; }
+    // rotate by q quarter turns: angle 2 pi m/256 = q pi/2 + 2 pi r/256
+    for (int k = 0; k < q; ++k) {
+      const double t = c;
+      c = -s;
+      s = t;
+    }
+    h64[m] = make_double2(c, -s);  // exp(-i angle)
+    h32[m] = make_float2((float)c, (float)-s);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(g_tw32, h32, sizeof(h32));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(g_tw64, h64, sizeof(h64));
+  if (e != cudaSuccess) return e;
+  if ((e = attrs_all<float>()) != cudaSuccess) return e;
+  return attrs_all<double>();
+}
+
+// -------------------------------------------------------- auxiliaries ---
+
+__global__ void k_v_stats(const void* V, int vreal, int64_t n, double* partials) {
+  double vmax = 0.0, amin = 1e300, bad = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = vreal ? make_float2(reinterpret_cast<const float*>(V)[i], 0.f)
+                     : reinterpret_cast<const float2*>(V)[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) {
+      bad += 1.0;
+      continue;
+    }
+    const double vr = v.x, vi = v.y;
+    vmax = fmax(vmax, sqrt(vr * vr + vi * vi));
+    const double br = 1.0 - vr;                      // B = 1 - V
+    amin = fmin(amin, br / (br * br + vi * vi));     // Re 1/B
+  }
+  __shared__ double r0[8], r1[8], r2[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    amin = fmin(amin, __shfl_down_sync(0xffffffffu, amin, o));
+    bad += __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    r0[w] = vmax;
+    r1[w] = amin;
+    r2[w] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      r0[0] = fmax(r0[0], r0[i]);
+      r1[0] = fmin(r1[0], r1[i]);
+      r2[0] += r2[i];
+    }
+    partials[3 * blockIdx.x] = r0[0];
+    partials[3 * blockIdx.x + 1] = r1[0];
+    partials[3 * blockIdx.x + 2] = r2[0];
+  }
+}
+
+__global__ void k_v_stats_final(const double* partials, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double vmax = 0.0, amin = 1e300, bad = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    vmax = fmax(vmax, partials[3 * b]);
+    amin = fmin(amin, partials[3 * b + 1]);
+    bad += partials[3 * b + 2];
+  }
+  out[0] = vmax;
+  out[1] = amin;
+  out[2] = bad;
+}
+
+cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials, int nblocks,
+                           double* out, cudaStream_t s) {
+  k_v_stats<<<nblocks, 256, 0, s>>>(V, vreal, n, partials);
+  k_v_stats_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_axpy1(float2* x, const float2* z, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = x[i], b = z[i];
+    x[i] = make_float2(a.x + b.x, a.y + b.y);
+  }
+}
+
+cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_axpy1<<<(unsigned)blocks, 256, 0, s>>>(x, z, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_sum_pairs(const double* partials, int count, double* out) {
+  __shared__ double red[8];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < count; i += 256) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  const double sa = block_sum<256>(a, red);
+  const double sb = block_sum<256>(b, red);
+  if (threadIdx.x == 0) {
+    out[0] = sa;
+    out[1] = sb;
+  }
+}
+
+cudaError_t launch_sum_pairs(const double* partials, int count, double* out, cudaStream_t s) {
+  k_sum_pairs<<<1, 256, 0, s>>>(partials, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace usp

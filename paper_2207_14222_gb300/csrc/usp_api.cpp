@@ -1,0 +1,784 @@
+// usp_api.cpp -- the C ABI of include/usp.h: solver handles, the schedule of
+// one fixed-point iteration (paper Algorithm 1, forward-eliminated operator
+// of Sec. 2.1), the convergence loop and FP64 iterative refinement.
+//
+// Iterations are launched in CUDA graphs of `chunk` iterations.  Every
+// kernel reads a device-side done flag at entry, so iterations queued after
+// convergence cost only empty launches; the host reads the device state
+// once per group of graph launches (the only device-to-host sync of the
+// loop).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "usp.h"
+
+using namespace usp;
+
+// ------------------------------------------------------------- errors ---
+
+static thread_local std::string g_last_error;
+
+static usp_status fail(usp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = std::string(usp_status_string(st)) + ": " + buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                             \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      usp_status st_ = (e_ == cudaErrorMemoryAllocation) ? USP_ERR_OOM : USP_ERR_CUDA; \
+      return fail(st_, "%s failed: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                              \
+  } while (0)
+
+// ---------------------------------------------------- per-device init ---
+
+static std::mutex g_init_mu;
+static uint64_t g_init_mask = 0;
+
+static usp_status ensure_device_init() {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev < 64 && (g_init_mask >> dev) & 1ull) return USP_OK;
+  CUDA_TRY(init_twiddles());
+  if (dev < 64) g_init_mask |= (1ull << dev);
+  return USP_OK;
+}
+
+// ------------------------------------------------------------ solver ---
+
+struct GraphEntry {
+  const void* y;
+  const void* x;
+  int chunk;
+  cudaGraphExec_t exec;
+};
+
+struct usp_solver {
+  int ndim = 0;
+  int n[3] = {1, 1, 1};
+  int64_t N = 0;
+  double dx = 1.0;
+  usp_lsymbol sym{};
+  bool vreal = false;
+  double alpha = 0.0;
+  double vmax = 0.0;
+  usp_options opt{};
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  void* V = nullptr;
+  float2* buf = nullptr;           // FP32 scratch field
+  double* partials = nullptr;
+  int64_t npartials = 0;
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;     // pinned mirror
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double* red = nullptr;           // 4 doubles (device)
+  double* red_host = nullptr;      // 4 doubles (pinned)
+  float2* z = nullptr;             // refinement correction
+  float2* yp = nullptr;            // refinement source y - A x
+  double2* buf64 = nullptr;        // FP64 scratch field
+  float2* hy = nullptr;            // device copies for usp_solve_host
+  float2* hx = nullptr;
+  std::vector<GraphEntry> graphs;
+  std::vector<double> history;
+  Sym<float> symf{};
+  Sym<double> symd{};
+};
+
+static bool is_pow2_in_range(int64_t v) { return v >= 2 && v <= 256 && (v & (v - 1)) == 0; }
+
+static void free_graphs(usp_solver* s) {
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
+// ------------------------------------------------------ the schedule ---
+
+static int64_t rows_grid_f32(const usp_solver* s) {
+  const int nx = s->n[s->ndim - 1];
+  const int64_t nrows = s->N / nx;
+  const int F = rows_per_block_f32(nx);
+  return (nrows + F - 1) / F;
+}
+static int64_t rows_grid_f64(const usp_solver* s) {
+  const int nx = s->n[s->ndim - 1];
+  const int64_t nrows = s->N / nx;
+  const int F = rows_per_block_f64(nx);
+  return (nrows + F - 1) / F;
+}
+
+template <typename T>
+static ColsArgs<T> cols_args(const usp_solver* s, int axis, int mode, int mul, int flags,
+                             void* buf, const Sym<T>& sym) {
+  ColsArgs<T> c{};
+  c.mode = mode;
+  c.mul = mul;
+  c.flags = flags;
+  int64_t inner = 1, outer = 1;
+  for (int ax = axis + 1; ax < s->ndim; ++ax) inner *= s->n[ax];
+  for (int ax = 0; ax < axis; ++ax) outer *= s->n[ax];
+  c.inner = inner;
+  c.outer = outer;
+  c.inner_blocks = (inner + 31) / 32;
+  c.buf = buf;
+  c.st = s->st;
+  c.sym = sym;
+  return c;
+}
+
+// One pass of an iteration: a kernel launch plus what it moves.
+struct PassLaunch {
+  const char* name;
+  double bytes_per_point;  // algorithmic HBM bytes per grid point
+  std::function<cudaError_t(cudaStream_t)> go;
+};
+
+// Kernel launches issued by this library (graph launches count their nodes).
+static std::atomic<int64_t> g_launches{0};
+
+// The passes of one FP32 iteration (or of the reference pass) on the pencil
+// schedule.  y: source; xin/xout: iterate in/out (xin unused with F_XZERO).
+static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, const float2* xin,
+                                             float2* xout, int flags) {
+  std::vector<PassLaunch> P;
+  const int vflag = s->vreal ? F_VREAL : 0;
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0, ref = (flags & F_REF) != 0;
+  const int nd = s->ndim;
+  const int nx = s->n[nd - 1];
+  RowsArgs<float> r{};
+  r.flags = flags | vflag;
+  r.nrows = s->N / nx;
+  r.x_in = xin;
+  r.x_out = xout;
+  r.y = y;
+  r.V = s->V;
+  r.buf = s->buf;
+  r.partials = s->partials;
+  r.st = s->st;
+  r.hist = s->hist;
+  r.alpha = (float)s->alpha;
+  r.sym = s->symf;
+  r.mul = MUL_LINV;
+  const int64_t grid = rows_grid_f32(s);
+  const double pre_bytes = 8.0 + (xz ? 0.0 : 8.0 + vb);                 // y, x, V
+  const double post_bytes = vb + (xz ? 0.0 : 8.0) + (ref ? 0.0 : 8.0);   // V, x in, x out
+  if (nd == 1) {
+    r.mode = R_IN_PRE | R_FWD | R_MUL | R_INV | R_OUT_POST;
+    P.push_back({"rows_full", pre_bytes + post_bytes - (xz ? 0.0 : vb + 8.0),
+                 [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
+    return P;
+  }
+  RowsArgs<float> r1 = r;
+  r1.mode = R_IN_PRE | R_FWD | R_OUT_BUF;
+  P.push_back({"rows_pre_fwd", pre_bytes + 8.0,
+               [=](cudaStream_t t) { return launch_rows_f32(nx, r1, grid, t); }});
+  const int cflags = flags & ~F_XZERO & ~F_REF;
+  if (nd == 2) {
+    auto c = cols_args<float>(s, 0, COL_FWD_MUL_INV, MUL_LINV, cflags, s->buf, s->symf);
+    const int n0 = s->n[0];
+    P.push_back({"cols0_fwd_mul_inv", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n0, c, t); }});
+  } else {
+    const int n0 = s->n[0], n1 = s->n[1];
+    auto c1 = cols_args<float>(s, 1, COL_FWD, MUL_LINV, cflags, s->buf, s->symf);
+    auto c0 = cols_args<float>(s, 0, COL_FWD_MUL_INV, MUL_LINV, cflags, s->buf, s->symf);
+    auto c2 = cols_args<float>(s, 1, COL_INV, MUL_LINV, cflags, s->buf, s->symf);
+    P.push_back({"cols1_fwd", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n1, c1, t); }});
+    P.push_back({"cols0_fwd_mul_inv", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n0, c0, t); }});
+    P.push_back({"cols1_inv", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n1, c2, t); }});
+  }
+  RowsArgs<float> r2 = r;
+  r2.mode = R_IN_BUF | R_INV | R_OUT_POST;
+  P.push_back({"rows_inv_post", 8.0 + post_bytes,
+               [=](cudaStream_t t) { return launch_rows_f32(nx, r2, grid, t); }});
+  return P;
+}
+
+static std::vector<PassLaunch> iteration_passes(usp_solver* s, const float2* y, const float2* xin,
+                                                float2* xout, int flags) {
+  return pencil_passes(s, y, xin, xout, flags);
+}
+
+static cudaError_t enqueue_iteration(usp_solver* s, const float2* y, const float2* xin,
+                                     float2* xout, int flags, cudaStream_t strm,
+                                     bool count = true) {
+  for (auto& p : iteration_passes(s, y, xin, xout, flags)) {
+    cudaError_t e = p.go(strm);
+    if (e != cudaSuccess) return e;
+    if (count) g_launches.fetch_add(1);
+  }
+  return cudaSuccess;
+}
+
+// r = y - A x (or A x with apply_a) in FP64; norms into s->red[0..1].
+static usp_status enqueue_residual64(usp_solver* s, const float2* x, const float2* y, float2* rout,
+                                     bool apply_a) {
+  if (!s->buf64) CUDA_TRY(cudaMalloc(&s->buf64, sizeof(double2) * s->N));
+  const int vflag = s->vreal ? F_VREAL : 0;
+  const int nd = s->ndim;
+  const int nx = s->n[nd - 1];
+  RowsArgs<double> r{};
+  r.flags = F_NOSTATE | vflag | (apply_a ? F_APPLY_A : 0);
+  r.nrows = s->N / nx;
+  r.x_in = x;
+  r.y = y;
+  r.V = s->V;
+  r.buf = s->buf64;
+  r.r_out = rout;
+  r.partials = s->partials;
+  r.st = s->st;
+  r.sym = s->symd;
+  r.mul = MUL_L;
+  const int64_t grid = rows_grid_f64(s);
+  if (nd == 1) {
+    r.mode = R_IN_X | R_FWD | R_MUL | R_INV | R_OUT_RESID;
+    CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
+  } else {
+    r.mode = R_IN_X | R_FWD | R_OUT_BUF;
+    CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
+    if (nd == 2) {
+      auto c = cols_args<double>(s, 0, COL_FWD_MUL_INV, MUL_L, F_NOSTATE, s->buf64, s->symd);
+      CUDA_TRY(launch_cols_f64(s->n[0], c, s->stream));
+    } else {
+      auto c1 = cols_args<double>(s, 1, COL_FWD, MUL_L, F_NOSTATE, s->buf64, s->symd);
+      CUDA_TRY(launch_cols_f64(s->n[1], c1, s->stream));
+      auto c0 = cols_args<double>(s, 0, COL_FWD_MUL_INV, MUL_L, F_NOSTATE, s->buf64, s->symd);
+      CUDA_TRY(launch_cols_f64(s->n[0], c0, s->stream));
+      auto c2 = cols_args<double>(s, 1, COL_INV, MUL_L, F_NOSTATE, s->buf64, s->symd);
+      CUDA_TRY(launch_cols_f64(s->n[1], c2, s->stream));
+    }
+    r.mode = R_IN_BUF | R_INV | R_OUT_RESID;
+    CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
+  }
+  CUDA_TRY(launch_sum_pairs(s->partials, (int)grid, s->red, s->stream));
+  g_launches.fetch_add(nd == 1 ? 2 : (nd == 2 ? 4 : 6));
+  return USP_OK;
+}
+
+// --------------------------------------------------------- create etc. ---
+
+static void destroy_impl(usp_solver* s) {
+  if (!s) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_graphs(s);
+  cudaFree(s->V);
+  cudaFree(s->buf);
+  cudaFree(s->partials);
+  cudaFree(s->st);
+  cudaFreeHost(s->st_host);
+  cudaFree(s->hist);
+  cudaFree(s->red);
+  cudaFreeHost(s->red_host);
+  cudaFree(s->z);
+  cudaFree(s->yp);
+  cudaFree(s->buf64);
+  cudaFree(s->hy);
+  cudaFree(s->hx);
+  if (s->ev) cudaEventDestroy(s->ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  cudaSetDevice(cur);
+  delete s;
+}
+
+extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol* lsym,
+                                        const void* V, int32_t V_is_real, double alpha,
+                                        void* cuda_stream, usp_solver** out) {
+  if (!out) return fail(USP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !lsym || !V) return fail(USP_ERR_INVALID_ARG, "grid, lsym and V must be non-NULL");
+  if (grid->ndim < 1 || grid->ndim > 3)
+    return fail(USP_ERR_INVALID_ARG, "ndim must be 1, 2 or 3 (got %d)", grid->ndim);
+  if (!(grid->dx > 0.0) || !std::isfinite(grid->dx))
+    return fail(USP_ERR_INVALID_ARG, "dx must be finite and > 0");
+  int64_t N = 1;
+  for (int ax = 0; ax < grid->ndim; ++ax) {
+    if (grid->n[ax] < 1) return fail(USP_ERR_INVALID_ARG, "axis %d has length %lld", ax, (long long)grid->n[ax]);
+    if (!is_pow2_in_range(grid->n[ax]))
+      return fail(USP_ERR_UNSUPPORTED_SIZE, "axis %d length %lld is not a power of two in [2, 256]",
+                  ax, (long long)grid->n[ax]);
+    N *= grid->n[ax];
+  }
+  const double sv[4] = {lsym->a_re, lsym->a_im, lsym->b_re, lsym->b_im};
+  for (double v : sv)
+    if (!std::isfinite(v)) return fail(USP_ERR_INVALID_ARG, "symbol coefficients must be finite");
+  // Re(Lhat(p) + 1) > 0 on the grid: linear in |p|^2 in [0, ndim (pi/dx)^2].
+  const double p2max = grid->ndim * (M_PI / grid->dx) * (M_PI / grid->dx);
+  const double re0 = lsym->b_re + 1.0, re1 = lsym->a_re * p2max + lsym->b_re + 1.0;
+  if (!(re0 > 0.0) || !(re1 > 0.0))
+    return fail(USP_ERR_NOT_ACCRETIVE, "Re(Lhat(p)+1) <= 0 on the grid (%.3g at p=0, %.3g at |p|max)", re0, re1);
+  if (std::isnan(alpha) || std::isinf(alpha) || alpha > 2.0)
+    return fail(USP_ERR_ALPHA_RANGE, "alpha must be finite and in (0, 2] (or <= 0 for automatic)");
+  usp_status st0 = ensure_device_init();
+  if (st0 != USP_OK) return st0;
+
+  usp_solver* s = new usp_solver();
+  s->ndim = grid->ndim;
+  for (int ax = 0; ax < 3; ++ax) s->n[ax] = ax < grid->ndim ? (int)grid->n[ax] : 1;
+  s->N = N;
+  s->dx = grid->dx;
+  s->sym = *lsym;
+  s->vreal = V_is_real != 0;
+  s->user_stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&s->device);
+  // symbol in both precisions
+  s->symd.a_re = lsym->a_re; s->symd.a_im = lsym->a_im;
+  s->symd.b_re = lsym->b_re; s->symd.b_im = lsym->b_im;
+  s->symd.inv_n = 1.0 / (double)N;
+  s->symd.ndim = s->ndim;
+  for (int ax = 0; ax < 3; ++ax) {
+    s->symd.n[ax] = s->n[ax];
+    s->symd.ks[ax] = 2.0 * M_PI / (s->n[ax] * grid->dx);
+  }
+  s->symf.a_re = (float)lsym->a_re; s->symf.a_im = (float)lsym->a_im;
+  s->symf.b_re = (float)lsym->b_re; s->symf.b_im = (float)lsym->b_im;
+  s->symf.inv_n = (float)(1.0 / (double)N);
+  s->symf.ndim = s->ndim;
+  for (int ax = 0; ax < 3; ++ax) {
+    s->symf.n[ax] = s->n[ax];
+    s->symf.ks[ax] = (float)s->symd.ks[ax];
+  }
+
+#define CREATE_TRY(call)                                                           \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      usp_status st_ = (e_ == cudaErrorMemoryAllocation) ? USP_ERR_OOM : USP_ERR_CUDA; \
+      destroy_impl(s);                                                             \
+      return fail(st_, "%s failed: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                              \
+  } while (0)
+
+  CREATE_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+  CREATE_TRY(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+  const size_t vbytes = (s->vreal ? sizeof(float) : sizeof(float2)) * (size_t)N;
+  CREATE_TRY(cudaMalloc(&s->V, vbytes));
+  CREATE_TRY(cudaMalloc(&s->buf, sizeof(float2) * (size_t)N));
+  const int64_t g32 = rows_grid_f32(s), g64 = rows_grid_f64(s);
+  s->npartials = std::max<int64_t>({g32, 2 * g64, 3 * 1024, 64});
+  CREATE_TRY(cudaMalloc(&s->partials, sizeof(double) * s->npartials));
+  CREATE_TRY(cudaMalloc(&s->st, sizeof(DevState)));
+  CREATE_TRY(cudaMallocHost(&s->st_host, sizeof(DevState)));
+  CREATE_TRY(cudaMalloc(&s->red, 4 * sizeof(double)));
+  CREATE_TRY(cudaMallocHost(&s->red_host, 4 * sizeof(double)));
+  CREATE_TRY(cudaMemsetAsync(s->st, 0, sizeof(DevState), s->stream));
+
+  // copy V (ordered after the caller's queued work), then its statistics
+  CREATE_TRY(cudaEventRecord(s->ev, s->user_stream));
+  CREATE_TRY(cudaStreamWaitEvent(s->stream, s->ev, 0));
+  CREATE_TRY(launch_copy_bytes(s->V, V, vbytes, s->stream));
+  int nb = (int)std::min<int64_t>(1024, (N + 255) / 256);
+  CREATE_TRY(launch_v_stats(s->V, s->vreal, N, s->partials, nb, s->red, s->stream));
+  g_launches.fetch_add(2);
+  CREATE_TRY(cudaMemcpyAsync(s->red_host, s->red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CREATE_TRY(cudaStreamSynchronize(s->stream));
+  const double vmax = s->red_host[0], astar = s->red_host[1], bad = s->red_host[2];
+  if (bad > 0) {
+    destroy_impl(s);
+    return fail(USP_ERR_NONFINITE, "V holds %.0f non-finite values", bad);
+  }
+  if (!(vmax < 1.0)) {
+    destroy_impl(s);
+    return fail(USP_ERR_V_NOT_CONTRACTIVE, "max|V| = %.6g >= 1", vmax);
+  }
+  s->vmax = vmax;
+  s->alpha = alpha > 0.0 ? alpha : astar;
+  *out = s;
+  return USP_OK;
+#undef CREATE_TRY
+}
+
+extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* opt) {
+  if (!s || !opt) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 2)
+    return fail(USP_ERR_INVALID_ARG, "invalid option value");
+  s->opt = *opt;
+  return USP_OK;
+}
+
+extern "C" usp_status usp_solver_alpha(const usp_solver* s, double* alpha_out) {
+  if (!s || !alpha_out) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  *alpha_out = s->alpha;
+  return USP_OK;
+}
+
+extern "C" void usp_solver_destroy(usp_solver* s) { destroy_impl(s); }
+
+// -------------------------------------------------------------- solve ---
+
+static usp_status ensure_hist(usp_solver* s, int cap) {
+  if (s->hist_cap >= cap) return USP_OK;
+  cudaFree(s->hist);
+  s->hist = nullptr;
+  s->hist_cap = 0;
+  CUDA_TRY(cudaMalloc(&s->hist, sizeof(double) * (size_t)cap));
+  s->hist_cap = cap;
+  free_graphs(s);  // graphs captured the old pointer
+  return USP_OK;
+}
+
+static usp_status get_graph(usp_solver* s, const float2* y, float2* x, int chunk,
+                            cudaGraphExec_t* exec) {
+  for (auto& g : s->graphs)
+    if (g.y == y && g.x == x && g.chunk == chunk) {
+      *exec = g.exec;
+      return USP_OK;
+    }
+  if (s->graphs.size() >= 8) free_graphs(s);
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < chunk && e == cudaSuccess; ++i)
+    e = enqueue_iteration(s, y, x, x, 0, s->stream, false);
+  cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(USP_ERR_CUDA, "kernel launch during capture: %s", cudaGetErrorString(e));
+  }
+  CUDA_TRY(e2);
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, graph, 0);
+  cudaGraphDestroy(graph);
+  CUDA_TRY(e);
+  s->graphs.push_back({y, x, chunk, ge});
+  *exec = ge;
+  return USP_OK;
+}
+
+static usp_status read_state(usp_solver* s) {
+  CUDA_TRY(cudaMemcpyAsync(s->st_host, s->st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return USP_OK;
+}
+static usp_status write_state(usp_solver* s) {
+  CUDA_TRY(cudaMemcpyAsync(s->st, s->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s->stream));
+  return USP_OK;
+}
+
+// Run iterations on (y, x) until the device state says done.
+static usp_status run_phase(usp_solver* s, const float2* y, float2* x, bool zero_start) {
+  const int chunk = s->opt.chunk > 0 ? s->opt.chunk : 8;
+  // the first iteration is launched directly (it may start from x = 0)
+  {
+    cudaError_t e = enqueue_iteration(s, y, x, x, zero_start ? F_XZERO : 0, s->stream);
+    if (e != cudaSuccess) return fail(USP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+  }
+  const int64_t passes_per_it = (int64_t)iteration_passes(s, y, x, x, 0).size();
+  cudaGraphExec_t ge = nullptr;
+  usp_status st = get_graph(s, y, x, chunk, &ge);
+  if (st != USP_OK) return st;
+  int launches = 1;
+  int prev_it = 0;
+  double prev_r = 0.0;
+  // Every launched iteration either counts in `it` or finds done set, so
+  // more launched iterations than the remaining budget (plus a chunk of
+  // slack) means the device state machine is broken: stop, do not spin.
+  const int start_it = s->st_host->it;
+  const int64_t budget = (int64_t)(s->st_host->it_limit - start_it) + 2 * chunk + 1;
+  int64_t launched = 1;
+  for (;;) {
+    for (int k = 0; k < launches; ++k) CUDA_TRY(cudaGraphLaunch(ge, s->stream));
+    launched += (int64_t)launches * chunk;
+    g_launches.fetch_add((int64_t)launches * chunk * passes_per_it);
+    if ((st = read_state(s)) != USP_OK) return st;
+    const DevState& h = *s->st_host;
+    if (h.done) return USP_OK;
+    if (launched > budget)
+      return fail(USP_ERR_CUDA, "device iteration state did not stop (it=%d of %d)", h.it, h.it_limit);
+    // Estimate the iterations left from the observed contraction rate and
+    // size the next group of launches to overshoot by at most one chunk.
+    int want = 4 * launches;
+    if (prev_it > 0 && h.it > prev_it && h.last_r > 0 && prev_r > h.last_r) {
+      const double rate = std::pow(h.last_r / prev_r, 1.0 / (h.it - prev_it));
+      const double left = std::log(std::max(h.tol, 1e-300) / h.last_r) / std::log(rate);
+      want = (int)std::ceil(std::max(1.0, left) / chunk);
+    }
+    prev_it = h.it;
+    prev_r = h.last_r;
+    launches = std::min(std::max(want, 1), std::max(1, 512 / chunk));
+    const int left_it = h.it_limit - h.it;
+    launches = std::min(launches, std::max(1, (left_it + chunk - 1) / chunk));
+  }
+}
+
+static usp_status solve_impl(usp_solver* s, const float2* y, float2* x, int use_x0, double tol,
+                             int maxit, double ref_norm, usp_result* out) {
+  usp_status st;
+  if ((st = ensure_hist(s, maxit)) != USP_OK) return st;
+  const bool refine = s->opt.plain == 0;
+  const int max_ref = s->opt.max_refinements > 0 ? s->opt.max_refinements : 4;
+
+  DevState& h = *s->st_host;
+  std::memset(&h, 0, sizeof h);
+  h.it_limit = maxit;
+  h.ref = ref_norm > 0 ? ref_norm : 0.0;
+  h.tol = tol;
+  if ((st = write_state(s)) != USP_OK) return st;
+
+  int refinements = 0;
+  bool stagnated = false;
+  bool skip = false;
+  if (use_x0 && !(ref_norm > 0)) {
+    // ||B (L+I)^-1 y||: Delta at x = 0, no update (Algorithm 1's denominator)
+    cudaError_t e = enqueue_iteration(s, y, x, x, F_XZERO | F_REF, s->stream);
+    if (e != cudaSuccess) return fail(USP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    if ((st = read_state(s)) != USP_OK) return st;
+    skip = h.done != 0;  // non-finite y
+  }
+
+  const float2* cy = y;  // source of the current phase
+  float2* cx = x;        // unknown of the current phase (x, then the correction z)
+  bool zero_start = !use_x0;
+  while (!skip && h.it < maxit) {
+    const bool can_refine = refine && refinements < max_ref;
+    h.done = 0;
+    h.status = ST_RUNNING;
+    h.phase_start = h.it;
+    h.tol = (can_refine && refinements == 0) ? 8.0 * tol : tol;
+    h.stall_window = can_refine ? 64 : 0;
+    if ((st = write_state(s)) != USP_OK) return st;
+    if ((st = run_phase(s, cy, cx, zero_start)) != USP_OK) return st;
+    if (cx != x) {
+      CUDA_TRY(launch_axpy1(x, cx, s->N, s->stream));  // x = x_b + z
+      g_launches.fetch_add(1);
+    }
+    const int stt = h.status;
+    stagnated = (stt == ST_STAGNATED);
+    if (stt == ST_NONFINITE || stt == ST_DIVERGED || stt == ST_MAXIT) break;
+    if (h.last_r < tol || h.ref == 0.0) break;  // converged
+    if (!can_refine) break;
+    // Refinement: Delta(x_b + z; y) = Delta(z; y - A x_b) exactly because
+    // A + B = L + I, so the same FP32 iteration continues on z with the
+    // source y - A x_b formed in FP64.
+    if (!s->z) CUDA_TRY(cudaMalloc(&s->z, sizeof(float2) * s->N));
+    if (!s->yp) CUDA_TRY(cudaMalloc(&s->yp, sizeof(float2) * s->N));
+    if ((st = enqueue_residual64(s, x, y, s->yp, false)) != USP_OK) return st;
+    ++refinements;
+    cy = s->yp;
+    cx = s->z;
+    zero_start = true;
+  }
+  if ((st = read_state(s)) != USP_OK) return st;
+
+  const int nit = std::min(h.it, s->hist_cap);
+  s->history.assign(nit, 0.0);
+  if (nit > 0) CUDA_TRY(cudaMemcpy(s->history.data(), s->hist, sizeof(double) * nit, cudaMemcpyDeviceToHost));
+
+  const bool converged = (h.status != ST_NONFINITE && h.status != ST_DIVERGED) &&
+                         (h.it > 0 || h.ref == 0.0) && (h.last_r < tol || h.ref == 0.0);
+  if (out) {
+    out->iterations = h.it;
+    out->converged = converged ? 1 : 0;
+    out->refinements = refinements;
+    out->stagnated = stagnated ? 1 : 0;
+    out->final_rel_residual = h.last_r;
+    out->ref_norm = h.ref;
+    out->alpha = s->alpha;
+  }
+  if (h.status == ST_NONFINITE) return fail(USP_ERR_NONFINITE, "non-finite value in y, x0 or an iterate");
+  if (h.status == ST_DIVERGED)
+    return fail(USP_ERR_DIVERGED, "||Delta|| grew from %.3g to %.3g (relative)", h.phase_first_r, h.last_r);
+  if (!converged)
+    return fail(USP_ERR_NOT_CONVERGED, "%s after %d iterations, residual %.3g",
+                stagnated ? "stagnated" : "iteration limit reached", h.it, h.last_r);
+  return USP_OK;
+}
+
+static usp_status check_solve_args(usp_solver* s, const void* y, void* x, double tol, int maxit) {
+  if (!s) return fail(USP_ERR_INVALID_ARG, "solver is NULL");
+  if (!y || !x) return fail(USP_ERR_INVALID_ARG, "y and x must be non-NULL");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(USP_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (maxit < 1) return fail(USP_ERR_INVALID_ARG, "maxit must be >= 1");
+  return USP_OK;
+}
+
+extern "C" usp_status usp_solve(usp_solver* s, const void* y, void* x, int32_t use_x0, double tol,
+                                int32_t maxit, double ref_norm, usp_result* out) {
+  usp_status st = check_solve_args(s, y, x, tol, maxit);
+  if (st != USP_OK) return st;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
+  // order after the caller's queued work on its stream
+  cudaError_t e = cudaEventRecord(s->ev, s->user_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev, 0);
+  if (e != cudaSuccess) st = fail(USP_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
+  if (st == USP_OK)
+    st = solve_impl(s, (const float2*)y, (float2*)x, use_x0, tol, maxit, ref_norm, out);
+  cudaStreamSynchronize(s->stream);
+  if (cur != s->device) cudaSetDevice(cur);
+  return st;
+}
+
+extern "C" usp_status usp_solve_host(usp_solver* s, const void* y_host, void* x_host,
+                                     int32_t use_x0, double tol, int32_t maxit, double ref_norm,
+                                     usp_result* out) {
+  usp_status st = check_solve_args(s, y_host, x_host, tol, maxit);
+  if (st != USP_OK) return st;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
+  const size_t bytes = sizeof(float2) * (size_t)s->N;
+  if (!s->hy) CUDA_TRY(cudaMalloc(&s->hy, bytes));
+  if (!s->hx) CUDA_TRY(cudaMalloc(&s->hx, bytes));
+  CUDA_TRY(cudaMemcpyAsync(s->hy, y_host, bytes, cudaMemcpyHostToDevice, s->stream));
+  if (use_x0) CUDA_TRY(cudaMemcpyAsync(s->hx, x_host, bytes, cudaMemcpyHostToDevice, s->stream));
+  st = solve_impl(s, s->hy, s->hx, use_x0, tol, maxit, ref_norm, out);
+  if (st == USP_OK || st == USP_ERR_NOT_CONVERGED) {
+    const std::string keep = g_last_error;
+    cudaError_t e = cudaMemcpyAsync(x_host, s->hx, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = fail(USP_ERR_CUDA, "copy back: %s", cudaGetErrorString(e));
+    else g_last_error = keep;
+  }
+  cudaStreamSynchronize(s->stream);
+  if (cur != s->device) cudaSetDevice(cur);
+  return st;
+}
+
+extern "C" usp_status usp_residual_history(const usp_solver* s, double* host_out, int32_t capacity,
+                                           int32_t* n_out) {
+  if (!s || !n_out) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  if (capacity > 0 && !host_out) return fail(USP_ERR_INVALID_ARG, "host_out is NULL");
+  const int n = (int)s->history.size();
+  const int m = std::min(n, std::max(0, (int)capacity));
+  if (m > 0) std::memcpy(host_out, s->history.data(), sizeof(double) * m);
+  *n_out = n;
+  return USP_OK;
+}
+
+static usp_status residual_common(usp_solver* s, const void* x, const void* y, void* r, bool apply_a,
+                                  double* rel_out) {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
+  cudaError_t e = cudaEventRecord(s->ev, s->user_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev, 0);
+  usp_status st = (e == cudaSuccess) ? USP_OK : fail(USP_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
+  if (st == USP_OK) st = enqueue_residual64(s, (const float2*)x, (const float2*)y, (float2*)r, apply_a);
+  if (st == USP_OK) {
+    e = cudaMemcpyAsync(s->red_host, s->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = fail(USP_ERR_CUDA, "residual: %s", cudaGetErrorString(e));
+  }
+  if (st == USP_OK && rel_out) {
+    const double nr = std::sqrt(s->red_host[0]), ny = std::sqrt(s->red_host[1]);
+    *rel_out = ny > 0 ? nr / ny : nr;
+  }
+  cudaStreamSynchronize(s->stream);
+  if (cur != s->device) cudaSetDevice(cur);
+  return st;
+}
+
+extern "C" usp_status usp_apply_A(usp_solver* s, const void* x, void* Ax) {
+  if (!s || !x || !Ax) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  if (x == Ax) return fail(USP_ERR_INVALID_ARG, "Ax may not alias x");
+  return residual_common(s, x, nullptr, Ax, true, nullptr);
+}
+
+extern "C" usp_status usp_residual(usp_solver* s, const void* x, const void* y, void* r,
+                                   double* rel_out) {
+  if (!s || !x || !y) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  if (r && (r == x || r == y)) return fail(USP_ERR_INVALID_ARG, "r may not alias x or y");
+  return residual_common(s, x, y, r, false, rel_out);
+}
+
+extern "C" const char* usp_status_string(usp_status st) {
+  switch (st) {
+    case USP_OK: return "USP_OK";
+    case USP_ERR_INVALID_ARG: return "USP_ERR_INVALID_ARG";
+    case USP_ERR_UNSUPPORTED_SIZE: return "USP_ERR_UNSUPPORTED_SIZE";
+    case USP_ERR_V_NOT_CONTRACTIVE: return "USP_ERR_V_NOT_CONTRACTIVE";
+    case USP_ERR_NOT_ACCRETIVE: return "USP_ERR_NOT_ACCRETIVE";
+    case USP_ERR_ALPHA_RANGE: return "USP_ERR_ALPHA_RANGE";
+    case USP_ERR_NOT_CONVERGED: return "USP_ERR_NOT_CONVERGED";
+    case USP_ERR_DIVERGED: return "USP_ERR_DIVERGED";
+    case USP_ERR_NONFINITE: return "USP_ERR_NONFINITE";
+    case USP_ERR_CUDA: return "USP_ERR_CUDA";
+    case USP_ERR_OOM: return "USP_ERR_OOM";
+  }
+  return "USP_ERR_UNKNOWN";
+}
+
+extern "C" const char* usp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int32_t usp_version(void) { return 100; }
+
+extern "C" int64_t usp_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int32_t iters,
+                                      usp_pass_time* out, int32_t capacity, int32_t* n_out) {
+  if (!s || !y || !x || !n_out || iters < 1) return fail(USP_ERR_INVALID_ARG, "bad argument");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
+  usp_status st = ensure_hist(s, iters + 1);
+  if (st != USP_OK) return st;
+  DevState& h = *s->st_host;
+  std::memset(&h, 0, sizeof h);
+  h.it_limit = iters + 1;
+  h.ref = 1.0;   // fixed denominator: nothing stops the timed iterations
+  h.tol = 0.0;
+  if ((st = write_state(s)) != USP_OK) return st;
+  auto passes = iteration_passes(s, (const float2*)y, (const float2*)x, (float2*)x, 0);
+  const size_t np = passes.size();
+  std::vector<cudaEvent_t> ev(2 * np, nullptr);
+  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+  std::vector<double> acc(np, 0.0);
+  usp_status res = USP_OK;
+  for (int it = 0; it < iters && res == USP_OK; ++it) {
+    for (size_t k = 0; k < np; ++k) {
+      cudaError_t e = cudaEventRecord(ev[2 * k], s->stream);
+      if (e == cudaSuccess) e = passes[k].go(s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], s->stream);
+      if (e != cudaSuccess) { res = fail(USP_ERR_CUDA, "timing launch: %s", cudaGetErrorString(e)); break; }
+      g_launches.fetch_add(1);
+    }
+    if (res != USP_OK) break;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) { res = fail(USP_ERR_CUDA, "timing sync: %s", cudaGetErrorString(e)); break; }
+    for (size_t k = 0; k < np; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+      acc[k] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (res == USP_OK) {
+    const int m = std::min<int>((int)np, std::max(0, (int)capacity));
+    for (int k = 0; k < m; ++k) {
+      std::memset(out[k].name, 0, sizeof out[k].name);
+      std::strncpy(out[k].name, passes[k].name, sizeof out[k].name - 1);
+      out[k].launches = iters;
+      out[k].ms = acc[k] / iters;
+      out[k].bytes = passes[k].bytes_per_point * (double)s->N;
+    }
+    *n_out = (int32_t)np;
+  }
+  if (cur != s->device) cudaSetDevice(cur);
+  return res;
+}

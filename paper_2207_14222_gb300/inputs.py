@@ -166,6 +166,18 @@ def random_diffusion(shape, seed, sigma_px=2.0, median_eta=0.05, sigma_log=0.5,
                 S=_centre_point_source(shape, 1.0), dx=1.0, seed=seed)
 
 
+def white_helmholtz(shape, seed, contrast=0.3, absorption=0.3, k0=K0_QUARTER_WAVE):
+    """Unsmoothed random medium of any shape, including axes of length 2:
+    k^2 = k0^2 (n^2 + i kappa) with n - 1 and kappa uniform per pixel, and a
+    random complex source."""
+    rng = np.random.default_rng(seed)
+    n_index = 1.0 + contrast * rng.uniform(size=shape)
+    kappa = absorption * rng.uniform(size=shape)
+    S = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    return dict(kind="helmholtz", k2=k0 ** 2 * (n_index ** 2 + 1j * kappa), S=S, dx=1.0,
+                k0=k0, seed=seed)
+
+
 def random_field(shape, seed, complex_=True):
     """Standard normal (complex) test vector."""
     rng = np.random.default_rng(seed)

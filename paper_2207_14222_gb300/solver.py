@@ -1,0 +1,166 @@
+"""Python front end of the GB300 solver: torch tensors in, torch tensors out.
+
+Marshals arguments to the C ABI (include/usp.h); PyTorch provides device
+memory and streams only.  There is no CPU path: without the built library
+or a CUDA device every call raises.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import Grid, LSymbol, Options, Result, check
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_launches():
+    """Kernel launches issued by the library so far in this process."""
+    return int(_lib.lib().usp_kernel_launches())
+
+
+class Solver:
+    """Fixed-point iteration with the universal split preconditioner for the
+    canonical system (L + V) x = y (Algorithm 1, forward-eliminated form).
+
+    shape : grid shape (1-3 axes, each a power of two in [2, 256]), last axis
+            fastest.
+    a, b  : symbol Lhat(p) = a |p|^2 + b (complex).
+    V     : CUDA tensor of the potential, complex64 (or float32 for a real
+            potential), copied at construction.
+    alpha : step size; <= 0 selects Re[B^-1] = min Re 1/(1 - V).
+    plain : True runs Algorithm 1 exactly (no FP64 refinement).
+    schedule : 0 auto, 1 pencil passes, 2 fused two-pass 3-D schedule.
+    """
+
+    def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
+                 schedule=0, chunk=0, max_refinements=0):
+        import torch
+        L = _lib.lib()
+        if not V.is_cuda:
+            raise ValueError("V must be a CUDA tensor")
+        if V.dtype not in (torch.complex64, torch.float32):
+            raise ValueError("V must be complex64 or float32")
+        V = V.contiguous()
+        self.shape = tuple(int(n) for n in shape)
+        if int(np.prod(self.shape)) != V.numel():
+            raise ValueError("V has %d elements, grid %s" % (V.numel(), self.shape))
+        self.device = V.device
+        g = Grid()
+        g.ndim = len(self.shape)
+        for i in range(3):
+            g.n[i] = self.shape[i] if i < len(self.shape) else 1
+        g.dx = float(dx)
+        sym = LSymbol(complex(a).real, complex(a).imag, complex(b).real, complex(b).imag)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self._stream = stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(L.usp_solver_create(ctypes.byref(g), ctypes.byref(sym), _ptr(V),
+                                      int(V.dtype == torch.float32), float(alpha),
+                                      ctypes.c_void_p(stream), ctypes.byref(h)))
+        self._h = h
+        self.set_options(plain=plain, schedule=schedule, chunk=chunk,
+                         max_refinements=max_refinements)
+
+    def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0):
+        o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements))
+        check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
+
+    @property
+    def alpha(self):
+        v = ctypes.c_double()
+        check(_lib.lib().usp_solver_alpha(self._h, ctypes.byref(v)))
+        return v.value
+
+    def solve(self, y, x=None, tol=1e-6, maxit=10000, ref_norm=0.0, use_x0=False,
+              allow_not_converged=True):
+        """Run the iteration; returns (x, result dict).  ``x`` (a CUDA
+        complex64 tensor) is updated in place and holds x0 if use_x0."""
+        import torch
+        y = y.contiguous()
+        if x is None:
+            x = torch.empty_like(y)
+            use_x0 = False
+        res = Result()
+        allow = (_lib.OK, _lib.ERR_NOT_CONVERGED) if allow_not_converged else (_lib.OK,)
+        with torch.cuda.device(self.device):
+            st = _lib.lib().usp_solve(self._h, _ptr(y), _ptr(x), int(bool(use_x0)), float(tol),
+                                      int(maxit), float(ref_norm), ctypes.byref(res))
+        check(st, allow)
+        d = res.as_dict()
+        d["status"] = _lib.STATUS[st]
+        return x, d
+
+    def solve_host(self, y_host, x_host, tol=1e-6, maxit=10000, ref_norm=0.0, use_x0=False):
+        """Same solve with host (CPU, ideally pinned) complex64 tensors."""
+        res = Result()
+        st = _lib.lib().usp_solve_host(self._h, _ptr(y_host), _ptr(x_host), int(bool(use_x0)),
+                                       float(tol), int(maxit), float(ref_norm),
+                                       ctypes.byref(res))
+        check(st, (_lib.OK, _lib.ERR_NOT_CONVERGED))
+        d = res.as_dict()
+        d["status"] = _lib.STATUS[st]
+        return x_host, d
+
+    def history(self):
+        n = ctypes.c_int32()
+        check(_lib.lib().usp_residual_history(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, np.float64)
+        if n.value:
+            check(_lib.lib().usp_residual_history(
+                self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                ctypes.byref(n)))
+        return out
+
+    def time_passes(self, y, x, iters=10):
+        """Per-kernel mean durations (CUDA events) of one iteration's
+        kernels; returns a list of dicts {name, ms, bytes, launches}."""
+        import torch
+        out = (_lib.PassTime * 16)()
+        n = ctypes.c_int32()
+        with torch.cuda.device(self.device):
+            check(_lib.lib().usp_time_passes(self._h, _ptr(y), _ptr(x), int(iters), out, 16,
+                                             ctypes.byref(n)))
+        return [dict(name=out[i].name.decode(), ms=out[i].ms, bytes=out[i].bytes,
+                     launches=out[i].launches) for i in range(n.value)]
+
+    def apply_A(self, x):
+        """A x = L x + V x in FP64 arithmetic (complex64 in and out)."""
+        import torch
+        x = x.contiguous()
+        out = torch.empty_like(x)
+        with torch.cuda.device(self.device):
+            check(_lib.lib().usp_apply_A(self._h, _ptr(x), _ptr(out)))
+        return out
+
+    def residual(self, x, y):
+        """(y - A x, ||y - A x|| / ||y||), FP64 arithmetic."""
+        import torch
+        x, y = x.contiguous(), y.contiguous()
+        r = torch.empty_like(x)
+        rel = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            check(_lib.lib().usp_residual(self._h, _ptr(x), _ptr(y), _ptr(r), ctypes.byref(rel)))
+        return r, rel.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().usp_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,121 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/usp.h declares, rejects bad arguments before touching the device,
+and its host-side canonical form agrees with the oracle's."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import canon as ocanon
+from paper_2207_14222_gb300 import _lib, inputs
+from paper_2207_14222_gb300 import build as pkg_build
+from paper_2207_14222_gb300 import canon as pcanon
+
+
+@pytest.fixture(scope="module")
+def L():
+    pkg_build.build()
+    return _lib.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = _lib.header_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding declares a signature for every one of them
+    assert set(names) == set(_lib._SIGNATURES), set(names) ^ set(_lib._SIGNATURES)
+
+
+def test_status_strings(L):
+    for code, name in _lib.STATUS.items():
+        assert L.usp_status_string(code).decode() == name
+    assert L.usp_version() >= 100
+
+
+def _grid(shape, dx=1.0):
+    g = _lib.Grid()
+    g.ndim = len(shape)
+    for i, n in enumerate(shape[:3]):
+        g.n[i] = n
+    g.dx = dx
+    return g
+
+
+def _create(L, shape, sym=(0.0, 0.3, 0.2, -0.5), V=1, alpha=0.0, dx=1.0):
+    g = _grid(shape, dx)
+    s = _lib.LSymbol(*sym)
+    h = ctypes.c_void_p()
+    st = L.usp_solver_create(ctypes.byref(g), ctypes.byref(s), ctypes.c_void_p(V), 0,
+                             alpha, None, ctypes.byref(h))
+    return st
+
+
+@pytest.mark.parametrize("shape, expect", [
+    ((), _lib.ERR_INVALID_ARG),                 # ndim 0
+    ((4, 4, 4, 4), _lib.ERR_INVALID_ARG),       # ndim 4
+    ((0, 8), _lib.ERR_INVALID_ARG),             # empty axis
+    ((100,), _lib.ERR_UNSUPPORTED_SIZE),        # not a power of two
+    ((512, 2), _lib.ERR_UNSUPPORTED_SIZE),      # above 256
+    ((1, 8), _lib.ERR_UNSUPPORTED_SIZE),        # length-1 axis
+])
+def test_create_rejects_bad_grids(L, shape, expect):
+    assert _create(L, shape) == expect
+
+
+def test_create_rejects_bad_arguments(L):
+    assert _create(L, (8, 8), V=0) == _lib.ERR_INVALID_ARG                 # NULL V
+    assert _create(L, (8, 8), dx=0.0) == _lib.ERR_INVALID_ARG
+    assert _create(L, (8, 8), dx=float("nan")) == _lib.ERR_INVALID_ARG
+    # Re(Lhat + 1) <= 0 somewhere on the grid (Corollary needs Re[L+I] > 0)
+    assert _create(L, (8, 8), sym=(0.0, 1.0, -1.5, 0.0)) == _lib.ERR_NOT_ACCRETIVE
+    assert _create(L, (8, 8), sym=(-1.0, 0.0, 0.0, 0.0)) == _lib.ERR_NOT_ACCRETIVE
+    assert _create(L, (8, 8), sym=(float("inf"), 0, 0, 0)) == _lib.ERR_INVALID_ARG
+    assert _create(L, (8, 8), alpha=2.5) == _lib.ERR_ALPHA_RANGE
+    assert _create(L, (8, 8), alpha=float("nan")) == _lib.ERR_ALPHA_RANGE
+    assert "alpha" in _lib.last_error()
+
+
+def test_null_handles(L):
+    r = _lib.Result()
+    assert L.usp_solve(None, None, None, 0, 1e-6, 10, 0.0, ctypes.byref(r)) == _lib.ERR_INVALID_ARG
+    n = ctypes.c_int32()
+    assert L.usp_residual_history(None, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID_ARG
+    L.usp_solver_destroy(None)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: inputs.helmholtz_2d(64, 2, abl_width=8),
+    lambda: inputs.random_helmholtz((8, 16, 16), 5),
+])
+def test_canonical_helmholtz_matches_oracle(L, make):
+    prob = make()
+    p = pcanon.canonical(prob)
+    o = ocanon.canonical(prob)
+    assert p["bias"] == pytest.approx(o["bias"], rel=1e-12, abs=1e-12)
+    assert p["c"] == pytest.approx(o["c"], rel=1e-12)
+    assert p["a"] == pytest.approx(o["a"], rel=1e-12)
+    assert p["b"] == pytest.approx(o["b"], rel=1e-12)
+    # complex64 outputs equal the rounded FP64 values to float rounding
+    assert np.max(np.abs(p["V"] - o["V"])) <= 1e-7 * np.max(np.abs(o["V"]))
+    assert np.max(np.abs(p["y"] - o["y"])) <= 1e-7 * np.max(np.abs(o["y"]))
+    assert np.max(np.abs(p["V"])) == pytest.approx(0.95, rel=1e-6)
+
+
+def test_canonical_diffusion_matches_oracle(L):
+    prob = inputs.random_diffusion((16, 8, 8), 6)
+    p = pcanon.canonical(prob)
+    o = ocanon.canonical(prob)
+    assert p["V"].dtype == np.float32
+    assert p["c"].real == pytest.approx(o["c"], rel=1e-12)
+    assert p["a"] == pytest.approx(o["a"], rel=1e-12)
+    assert p["b"] == pytest.approx(o["b"], rel=1e-12)
+    assert np.max(np.abs(p["V"] - o["V"].real)) <= 1e-7
+
+
+def test_canonical_rejects_homogeneous_medium(L):
+    prob = inputs.random_helmholtz((8, 8), 1)
+    prob["k2"] = np.full((8, 8), 2.0 + 0.1j)
+    with pytest.raises(_lib.UspError):
+        pcanon.canonical(prob)

@@ -1,0 +1,318 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Both sides get the same inputs: the oracle's canonical V and y rounded to
+complex64 (float32 for a real potential), upcast again for the oracle, so
+the comparison measures the solver's arithmetic only.
+
+Tolerance: relative L2 error <= 1e-5 on the iterate after the same number
+of iterations (the complex64 bar), and 1e-4 relative on the residual
+history while it is far above the FP32 floor.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import canon as ocanon
+from oracle import usp_oracle as uo
+from paper_2207_14222_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-5
+TOL_HIST = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2207_14222_gb300 import build
+    build.build()
+    _lib.lib()
+    return torch
+
+
+def _prep(prob, vreal=False):
+    cf = ocanon.canonical(prob)
+    if vreal:
+        V = cf["V"].real.astype(np.float32)
+    else:
+        V = cf["V"].astype(np.complex64)
+    y = cf["y"].astype(np.complex64)
+    return cf, V, y
+
+
+def _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha=0.0, schedule=0):
+    from paper_2207_14222_gb300.solver import Solver
+    dev = torch.device("cuda:0")
+    Vd = torch.from_numpy(V).to(dev)
+    yd = torch.from_numpy(y).to(dev)
+    with Solver(shape, cf["a"], cf["b"], Vd, alpha=alpha, dx=cf["dx"], plain=True,
+                schedule=schedule) as s:
+        x, res = s.solve(yd, tol=0.0, maxit=n_iter)
+        hist = s.history()
+        torch.cuda.synchronize()
+        return x.cpu().numpy().astype(np.complex128), res, hist
+
+
+def _oracle_iterate(shape, cf, V, y, n_iter, alpha):
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    return uo.iterate(V.astype(np.complex128), y.astype(np.complex128), Lh, alpha, n_iter)
+
+
+def _check_trajectory(torch, shape, prob, n_iter, vreal=False, alpha=0.0):
+    cf, V, y = _prep(prob, vreal)
+    xg, res, hg = _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha)
+    assert res["iterations"] == n_iter
+    a = res["alpha"]
+    if alpha <= 0:
+        assert a == pytest.approx(uo.alpha_star(V.astype(np.complex128)), rel=1e-6)
+    xo, ho = _oracle_iterate(shape, cf, V, y, n_iter, a)
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert err <= TOL_X, err
+    far = ho > 1e-3
+    herr = np.max(np.abs(hg[far] - ho[far]) / ho[far])
+    assert herr <= TOL_HIST, herr
+    assert res["ref_norm"] == pytest.approx(
+        uo.reference_norm(y.astype(np.complex128), V.astype(np.complex128),
+                          uo.lhat(shape, cf["dx"], cf["a"], cf["b"])), rel=1e-5)
+    return err
+
+
+# ------------------------------------------------------------- shapes ---
+
+@pytest.mark.parametrize("shape", [(2,), (8,), (256,)])
+def test_parity_1d(torch_cuda, shape):
+    _check_trajectory(torch_cuda, shape, inputs.white_helmholtz(shape, 1), 40)
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (4, 32), (16, 256), (256, 8), (64, 64)])
+def test_parity_2d_shapes(torch_cuda, shape):
+    _check_trajectory(torch_cuda, shape, inputs.white_helmholtz(shape, 2), 30)
+
+
+def test_parity_2d_helmholtz_128(torch_cuda):
+    """The 2-D 128x128 workload (sigma 4 px, amplitude 0.3, ABL 16 px,
+    centre point source), 300 iterations."""
+    prob = inputs.helmholtz_2d(128, seed=0)
+    _check_trajectory(torch_cuda, (128, 128), prob, 300)
+
+
+@pytest.mark.parametrize("shape", [(2, 4, 8), (8, 16, 32), (32, 32, 32), (16, 2, 64),
+                                   (4, 256, 2), (64, 64, 64)])
+def test_parity_3d_shapes(torch_cuda, shape):
+    _check_trajectory(torch_cuda, shape, inputs.white_helmholtz(shape, 3), 25)
+
+
+def test_parity_3d_helmholtz_64(torch_cuda):
+    """The 3-D Helmholtz medium generator at 64^3 (lengths scaled by 1/4)."""
+    prob = inputs.helmholtz_3d(64, seed=0)
+    _check_trajectory(torch_cuda, (64, 64, 64), prob, 100)
+
+
+def test_parity_diffusion_real_potential(torch_cuda):
+    prob = inputs.random_diffusion((32, 32, 32), 4, sigma_px=2.0)
+    _check_trajectory(torch_cuda, (32, 32, 32), prob, 60, vreal=True)
+    prob = inputs.random_diffusion((64, 128), 5, sigma_px=3.0)
+    _check_trajectory(torch_cuda, (64, 128), prob, 60, vreal=True)
+
+
+def test_parity_fixed_alpha(torch_cuda):
+    prob = inputs.random_helmholtz((32, 64), 6, sigma_px=2.0)
+    for alpha in (1.0, 0.7):
+        _check_trajectory(torch_cuda, (32, 64), prob, 40, alpha=alpha)
+
+
+# ------------------------------------------------------ full solves ---
+
+def test_solve_to_tolerance_with_refinement(torch_cuda):
+    """GPU (FP32 + FP64 refinement) to 1e-6 against the oracle's solve to
+    the same tolerance: same iteration count within a few, same field."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (128, 128)
+    cf, V, y = _prep(inputs.helmholtz_2d(128, seed=1))
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev)) as s:
+        x, res = s.solve(torch.from_numpy(y).to(dev), tol=1e-6, maxit=5000,
+                         allow_not_converged=False)
+        xg = x.cpu().numpy().astype(np.complex128)
+        hg = s.history()
+        _, rel = s.residual(x, torch.from_numpy(y).to(dev))
+    assert res["converged"] == 1 and res["final_rel_residual"] < 1e-6
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    V64, y64 = V.astype(np.complex128), y.astype(np.complex128)
+    xo, ho, ok = uo.solve(V64, y64, Lh, res["alpha"], 1e-6, 5000)
+    assert ok
+    # the refinement restart may shift the stopping step by a few iterations
+    assert abs(res["iterations"] - len(ho)) <= max(5, len(ho) // 50)
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL_X
+    # the true preconditioned residual of the returned field
+    d = uo.residual_delta(xg, y64, V64, Lh)
+    assert np.linalg.norm(d) / res["ref_norm"] < 1.5e-6
+    assert rel == pytest.approx(uo.relative_residual(xg, y64, V64, Lh), rel=1e-3)
+    assert len(hg) == res["iterations"]
+
+
+def test_plain_mode_reports_stagnation_floor(torch_cuda):
+    """Plain FP32 Algorithm 1 with a tolerance below its rounding floor ends
+    NOT_CONVERGED at maxit, x still valid (close to the oracle's)."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (64, 64)
+    cf, V, y = _prep(inputs.helmholtz_2d(64, seed=2, abl_width=8))
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), plain=True) as s:
+        x, res = s.solve(torch.from_numpy(y).to(dev), tol=1e-12, maxit=600)
+    assert res["status"] == "USP_ERR_NOT_CONVERGED" and res["iterations"] == 600
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    xo, _, _ = uo.solve(V.astype(np.complex128), y.astype(np.complex128), Lh, res["alpha"],
+                        1e-10, 5000)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-4
+
+
+def test_warm_start_continues_trajectory(torch_cuda):
+    """x0 from 40 iterations + 40 more with the stored reference norm equals
+    80 oracle iterations; with ref_norm <= 0 the reference pass recomputes
+    ||B (L+I)^-1 y|| (Algorithm 1's denominator)."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (32, 32, 32)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 9, sigma_px=2.0))
+    dev = torch.device("cuda:0")
+    yd = torch.from_numpy(y).to(dev)
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), plain=True) as s:
+        x, r1 = s.solve(yd, tol=0.0, maxit=40)
+        x, r2 = s.solve(yd, x=x, use_x0=True, tol=0.0, maxit=40, ref_norm=r1["ref_norm"])
+        x2 = x.clone()
+        _, r3 = s.solve(yd, x=x2, use_x0=True, tol=0.0, maxit=1)
+    xo, ho = _oracle_iterate(shape, cf, V, y, 80, r1["alpha"])
+    assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= TOL_X
+    assert r3["ref_norm"] == pytest.approx(r1["ref_norm"], rel=1e-5)
+
+
+def test_host_api_matches_device_api(torch_cuda):
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (64, 64)
+    cf, V, y = _prep(inputs.helmholtz_2d(64, seed=3, abl_width=8))
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev)) as s:
+        xd, rd = s.solve(torch.from_numpy(y).to(dev), tol=1e-6, maxit=3000)
+        yh = torch.from_numpy(y).pin_memory()
+        xh = torch.empty_like(yh).pin_memory()
+        xh, rh = s.solve_host(yh, xh, tol=1e-6, maxit=3000)
+    assert rd["iterations"] == rh["iterations"]
+    assert torch.equal(xd.cpu(), xh)
+
+
+def test_deterministic(torch_cuda):
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (16, 32, 64)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 10))
+    dev = torch.device("cuda:0")
+    out = []
+    for _ in range(2):
+        with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev)) as s:
+            x, r = s.solve(torch.from_numpy(y).to(dev), tol=1e-5, maxit=2000)
+            out.append((x.cpu(), s.history()))
+    assert torch.equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_apply_A_and_residual_fp64(torch_cuda):
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    for shape, vreal in (((128,), False), ((32, 64), False), ((16, 16, 32), True)):
+        if vreal:
+            cf, V, y = _prep(inputs.random_diffusion(shape, 11), vreal=True)
+        else:
+            cf, V, y = _prep(inputs.random_helmholtz(shape, 11))
+        x = inputs.random_field(shape, 12).astype(np.complex64)
+        dev = torch.device("cuda:0")
+        with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev)) as s:
+            Ax = s.apply_A(torch.from_numpy(x).to(dev)).cpu().numpy()
+            r, rel = s.residual(torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev))
+        Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+        Ao = uo.apply_A(x.astype(np.complex128), V.astype(np.complex128), Lh)
+        assert np.linalg.norm(Ax - Ao) / np.linalg.norm(Ao) < 1e-6
+        ro = y.astype(np.complex128) - Ao
+        assert np.linalg.norm(r.cpu().numpy() - ro) / np.linalg.norm(ro) < 1e-6
+        assert rel == pytest.approx(np.linalg.norm(ro) / np.linalg.norm(y), rel=1e-9)
+
+
+# ------------------------------------------------------ edge cases ---
+
+def _solver(torch, shape, cf, V, **kw):
+    from paper_2207_14222_gb300.solver import Solver
+    return Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to("cuda:0"), **kw)
+
+
+def test_edge_maxit_one_and_zero_source(torch_cuda):
+    torch = torch_cuda
+    shape = (16, 16)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 13))
+    with _solver(torch, shape, cf, V, plain=True) as s:
+        x, r = s.solve(torch.from_numpy(y).cuda(), tol=1e-6, maxit=1)
+        assert r["status"] == "USP_ERR_NOT_CONVERGED" and r["iterations"] == 1
+        xo, _ = _oracle_iterate(shape, cf, V, y, 1, r["alpha"])
+        assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) < TOL_X
+        z = torch.zeros(shape, dtype=torch.complex64, device="cuda:0")
+        x, r = s.solve(z, tol=1e-6, maxit=10)
+        assert r["status"] == "USP_OK" and r["converged"] == 1
+        assert torch.count_nonzero(x).item() == 0
+
+
+def test_edge_nonfinite_source_and_potential(torch_cuda):
+    torch = torch_cuda
+    shape = (8, 32)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 14))
+    yb = y.copy()
+    yb[3, 5] = np.nan
+    with _solver(torch, shape, cf, V) as s:
+        with pytest.raises(_lib.UspError) as e:
+            s.solve(torch.from_numpy(yb).cuda(), tol=1e-6, maxit=50)
+        assert e.value.status == _lib.ERR_NONFINITE
+    Vb = V.copy()
+    Vb[0, 0] = np.inf
+    with pytest.raises(_lib.UspError) as e:
+        _solver(torch, shape, cf, Vb)
+    assert e.value.status == _lib.ERR_NONFINITE
+
+
+def test_edge_potential_not_contractive(torch_cuda):
+    torch = torch_cuda
+    shape = (8, 8)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 15))
+    with pytest.raises(_lib.UspError) as e:
+        _solver(torch, shape, cf, (V * 1.1).astype(np.complex64))
+    assert e.value.status == _lib.ERR_V_NOT_CONTRACTIVE
+
+
+def test_edge_non_accretive_diverges(torch_cuda):
+    """A = L + V with Re A < 0 everywhere (outside Thm 1): the iteration
+    grows and the solver reports USP_ERR_DIVERGED."""
+    torch = torch_cuda
+    shape = (16, 16)
+    rng = np.random.default_rng(16)
+    V = (0.1 + 0.05 * rng.uniform(size=shape)).astype(np.float32)
+    y = inputs.random_field(shape, 17).astype(np.complex64)
+    from paper_2207_14222_gb300.solver import Solver
+    with Solver(shape, 0.0, -0.5, torch.from_numpy(V).cuda(), alpha=1.0, plain=True) as s:
+        with pytest.raises(_lib.UspError) as e:
+            s.solve(torch.from_numpy(y).cuda(), tol=1e-6, maxit=500)
+    assert e.value.status == _lib.ERR_DIVERGED
+
+
+def test_residual_history_is_monotone(torch_cuda):
+    """Thm 1: ||Delta_i|| decreases monotonically (until the FP32 floor)."""
+    torch = torch_cuda
+    shape = (64, 64, 64)
+    cf, V, y = _prep(inputs.helmholtz_3d(64, seed=1))
+    with _solver(torch, shape, cf, V, plain=True) as s:
+        s.solve(torch.from_numpy(y).cuda(), tol=1e-5, maxit=2000)
+        h = s.history()
+    h = h[h > 2e-5]
+    assert np.all(np.diff(h) < 0)
