@@ -206,6 +206,34 @@ usp_status usp_canon_diffusion(const double* eta, double D, const double* S,
                                float* y_out, usp_lsymbol* lsym_out,
                                double* c_out, double* bias_out);
 
+/* ---- allocation-free solve (no counterpart in the paper) ----------------
+ *
+ * For callers that cannot allocate device memory -- e.g. a process whose
+ * device memory was handed to another allocator at start-up, or a hot loop
+ * that must not call cudaMalloc/cudaFree because they synchronise the
+ * device.  Runs plain Algorithm 1 (no FP64 refinement) from x = 0 on the
+ * caller's V, y and x, with all scratch (one field, partial sums, state,
+ * residual history) in a fixed area of USP_NOALLOC_BYTES compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Grids up to USP_NOALLOC_MAX_POINTS points and maxit up to
+ * USP_NOALLOC_MAX_ITERS; larger requests return USP_ERR_UNSUPPORTED_SIZE /
+ * USP_ERR_INVALID_ARG with a message (usp_last_error).  It calls no
+ * allocation routine.
+ *
+ * The first call on a device does a one-time set-up there (looks up the
+ * scratch area's device address, uploads the FFT twiddle tables): make that
+ * first call before any stream capture.  All calls share the one scratch
+ * area, whose contents persist between calls (each call rewrites what must
+ * start from zero); calls whose GPU work overlaps in time race on it, so
+ * serialise them.  Arguments as for usp_solver_create and usp_solve (device
+ * pointers V, y, x; x is output only).  Synchronous. */
+#define USP_NOALLOC_MAX_POINTS (1 << 19)
+#define USP_NOALLOC_MAX_ITERS 65536
+#define USP_NOALLOC_BYTES 4751872
+usp_status usp_solve_noalloc(const usp_grid* grid, const usp_lsymbol* lsym, const void* V,
+                             int32_t V_is_real, double alpha, const void* y, void* x,
+                             double tol, int32_t maxit, void* cuda_stream, usp_result* out);
+
 /* ---- measurement (no counterpart in the paper; used by the benchmark) -- */
 
 /* Mean duration of each kernel of one iteration. */

@@ -77,6 +77,9 @@ _SIGNATURES = {
                                       c_void_p, _P(LSymbol), c_void_p, c_void_p]),
     "usp_canon_diffusion": (c_int32, [c_void_p, c_double, c_void_p, c_int64, c_double,
                                       c_void_p, c_void_p, _P(LSymbol), c_void_p, c_void_p]),
+    "usp_solve_noalloc": (c_int32, [_P(Grid), _P(LSymbol), c_void_p, c_int32, c_double,
+                                    c_void_p, c_void_p, c_double, c_int32, c_void_p,
+                                    _P(Result)]),
     "usp_time_passes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, _P(PassTime),
                                   c_int32, _P(c_int32)]),
     "usp_kernel_launches": (c_int64, []),

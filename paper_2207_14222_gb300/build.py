@@ -25,6 +25,7 @@ SOURCES = [
     "fused3d_kernels.cu",
     "usp_api.cpp",
     "canon.cpp",
+    "noalloc.cu",
 ]
 
 

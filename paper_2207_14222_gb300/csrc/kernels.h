@@ -132,6 +132,8 @@ cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials
 cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s);
 // Sum `count` partial pairs (2 doubles per block) into out[2].
 cudaError_t launch_sum_pairs(const double* partials, int count, double* out, cudaStream_t s);
+// Record the message usp_last_error() returns on this thread (usp_api.cpp).
+void set_last_error(const char* fmt, ...);
 // Copy a real float32 or complex64 potential into solver storage.
 cudaError_t launch_copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t s);
 

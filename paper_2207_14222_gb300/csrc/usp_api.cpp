@@ -39,6 +39,15 @@ static usp_status fail(usp_status st, const char* fmt, ...) {
   return st;
 }
 
+void usp::set_last_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
 #define CUDA_TRY(call)                                                             \
   do {                                                                             \
     cudaError_t e_ = (call);                                                       \
