@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--maxit", type=int, default=20000)
     p.add_argument("--schedule", type=int, default=0)
     p.add_argument("--plain", action="store_true", help="time the plain FP32 iteration")
+    p.add_argument("--no-tma", action="store_true",
+                   help="strided-axis passes without TMA staging (comparison)")
     p.add_argument("--cpu-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, plain and roofline legs")
@@ -200,7 +202,8 @@ def run_ours(args):
     x = torch.empty_like(y)
 
     def step():
-        with Solver(shape, cf["a"], cf["b"], V, plain=args.plain, schedule=args.schedule) as s:
+        with Solver(shape, cf["a"], cf["b"], V, plain=args.plain, schedule=args.schedule,
+                    no_tma=args.no_tma) as s:
             _, r = s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
         return r
 
@@ -265,6 +268,7 @@ def run_ours(args):
                 "tol": args.tol,
                 "mode": "plain" if args.plain else "fp32+fp64-refinement",
                 "schedule": ["auto", "pencil", "fused"][args.schedule],
+                "tma": not args.no_tma,
                 "step": "create + solve to tol + destroy",
                 "l2": "inputs 384 MiB > L2, no flush",
                 "replicas": ws,
@@ -290,7 +294,7 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
     out = {}
     # per-kernel durations (CUDA events on the solver's stream) -> roofline
     xt = torch.empty_like(y)
-    with Solver(shape, cf["a"], cf["b"], V, schedule=args.schedule) as s:
+    with Solver(shape, cf["a"], cf["b"], V, schedule=args.schedule, no_tma=args.no_tma) as s:
         s.solve(y, x=xt, tol=0.0, maxit=5)  # warm
         passes = s.time_passes(y, xt, iters=20)
     per_it_ms = sum(p["ms"] for p in passes)

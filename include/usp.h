@@ -102,6 +102,9 @@ typedef struct {
   int32_t chunk;
   /* maximum FP64 refinements per solve; 0: default (4)                     */
   int32_t max_refinements;
+  /* 1: strided-axis passes load and store with plain global accesses
+   *    instead of TMA-staged tiles (for comparison); 0: TMA (default)      */
+  int32_t no_tma;
 } usp_options;
 
 typedef struct usp_solver usp_solver;

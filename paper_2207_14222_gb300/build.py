@@ -26,6 +26,7 @@ SOURCES = [
     "usp_api.cpp",
     "canon.cpp",
     "noalloc.cu",
+    "tma_kernels.cu",
 ]
 
 

@@ -2,6 +2,7 @@
 // and the CUDA kernels.  Not part of the public ABI (include/usp.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,7 +18,8 @@ enum DevStatus : int {
   ST_MAXIT = 2,       // it reached it_limit
   ST_NONFINITE = 3,   // NaN/Inf norm
   ST_DIVERGED = 4,    // ||Delta|| above 4x its first value in this phase
-  ST_STAGNATED = 5    // no 0.1% improvement over stall_window iterations
+  ST_STAGNATED = 5,   // no 0.1% improvement over stall_window iterations
+  ST_TIMEOUT = 6      // a bounded wait inside a kernel gave up (copy engine)
 };
 
 struct DevState {
@@ -43,7 +45,8 @@ enum : int {
   F_REF = 2,        // reference pass: Delta at x = 0, store ||Delta|| in ref, no update
   F_NOSTATE = 4,    // ignore the device state (stand-alone transforms)
   F_APPLY_A = 8,    // residual pass writes A x instead of y - A x
-  F_VREAL = 16      // V is float32 (real potential)
+  F_VREAL = 16,     // V is float32 (real potential)
+  F_CBLOCK = 32     // z pass over the column-block layout of the fused schedule
 };
 
 // Rows pass (transform along the contiguous last axis): a bit set of
@@ -57,7 +60,9 @@ enum RowMode : int {
   R_INV = 32,        // inverse transform
   R_OUT_BUF = 64,    // scratch row = result
   R_OUT_POST = 128,  // Delta = (1-V)(u - x); x += alpha Delta; ||Delta||^2 (fp32)
-  R_OUT_RESID = 256  // r = y - (u + V x)  [or A x = u + V x]; norms  (fp64)
+  R_OUT_RESID = 256, // r = y - (u + V x)  [or A x = u + V x]; norms  (fp64)
+  R_THEN_PRE_FWD = 512  // with R_OUT_POST: then t = (1-V) x_new + y and
+                        // the forward transform of the next iteration -> scratch
 };
 
 // Strided-axis pass modes.
@@ -113,6 +118,50 @@ struct ColsArgs {
   DevState* st;
   Sym<T> sym;
 };
+
+// Plane pass of the fused schedule (fused3d_kernels.cu), grids nz x 256 x 256.
+enum PlaneMode : int {
+  PL_PRE = 0,    // t = (1-V) x + y ; T = F_xy t           (phase prologue)
+  PL_FULL = 1,   // F_xy^-1 ; Delta, update, norm ; next t ; F_xy
+  PL_POST = 2    // F_xy^-1 ; Delta, norm (reference pass, no update)
+};
+
+struct PlaneArgs {
+  int mode;
+  int flags;
+  int nz;
+  const float2* x_in;
+  float2* x_out;
+  const float2* y;
+  const void* V;
+  float2* buf;          // column-block layout T[z][cb][y][xl]
+  const float2* tw;     // W_256^m table (device)
+  double* partials;     // one double per CTA
+  DevState* st;
+  double* hist;
+  float alpha;
+};
+
+cudaError_t plane_kernel_init();
+cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s);
+int plane_max_active_clusters();
+const float2* twiddle_table_f32();
+
+// Strided-axis pass with TMA-staged tiles (tma_kernels.cu).  The tensor map
+// views the field as [outer][N][inner] (3-D, 8-byte elements, box {32, N, 1}).
+struct ColsTmaArgs {
+  int mode;             // ColMode
+  int mul;              // MulKind
+  int flags;
+  int64_t inner_blocks; // ceil(inner / 32)
+  int64_t tiles;        // outer * inner_blocks
+  DevState* st;
+  const float2* tw;     // W_256^m table (device)
+  Sym<float> sym;
+};
+cudaError_t cols_tma_init();
+cudaError_t launch_cols_tma(int n, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
+                            cudaStream_t s);
 
 // Launchers (pencil_kernels.cu).  n = transform length (power of two, 2..256).
 cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaStream_t s);

@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "fft_core.cuh"
+#include "iteration_state.cuh"
 #include "kernels.h"
 
 namespace usp {
@@ -57,70 +58,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     for (int i = 0; i < THREADS / 32; ++i) s += red[i];
   }
   return s;  // valid in thread 0
-}
-
-// Iteration bookkeeping after ||Delta||^2 is known (Algorithm 1's test).
-__device__ void finalize_iteration(DevState* st, double* hist, double sumsq, int flags) {
-  const double nrm = sqrt(sumsq);
-  if (flags & F_REF) {
-    st->ref = nrm;
-    if (!isfinite(nrm)) {
-      st->status = ST_NONFINITE;
-      st->done = 1;
-    }
-    return;
-  }
-  if (st->it >= st->it_limit) {  // never write past the history buffer
-    st->status = ST_MAXIT;
-    st->done = 1;
-    return;
-  }
-  st->sumsq = sumsq;
-  if (!isfinite(nrm)) {
-    st->last_r = nrm;
-    st->status = ST_NONFINITE;
-    st->done = 1;
-    return;
-  }
-  double ref = st->ref;
-  if (ref <= 0.0) {  // x0 = 0: Delta_1 = B (L+I)^-1 y, the reference itself
-    ref = nrm;
-    st->ref = nrm;
-  }
-  const double r = ref > 0.0 ? nrm / ref : 0.0;
-  const int it = st->it;
-  hist[it] = r;
-  st->it = it + 1;
-  st->last_r = r;
-  if (it == st->phase_start) {
-    st->phase_first_r = r;
-    st->best_r = r;
-    st->best_it = it + 1;
-  }
-  if (r < st->tol || ref == 0.0) {
-    st->status = ST_CONVERGED;
-    st->done = 1;
-    return;
-  }
-  if (it > st->phase_start && r > 4.0 * st->phase_first_r) {
-    st->status = ST_DIVERGED;
-    st->done = 1;
-    return;
-  }
-  if (it + 1 >= st->it_limit) {
-    st->status = ST_MAXIT;
-    st->done = 1;
-    return;
-  }
-  if (st->stall_window > 0) {
-    if (r < st->best_r * (1.0 - 1e-3)) {
-      st->best_r = r;
-      st->best_it = it + 1;
-    } else if (it + 1 - st->best_it >= st->stall_window) {
-      st->status = ST_STAGNATED;
-      st->done = 1;
-    }
-  }
 }
 
 // Block partial of ||Delta||^2, then the last block to finish sums all
@@ -274,6 +211,7 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS) k_rows(const RowsArgs<T> 
   if (a.mode & R_OUT_POST) {
     // Delta = (1-V)(u - x) ; x += alpha Delta  (Algorithm 1)
     float acc = 0.f;
+    const bool then_pre = (a.mode & R_THEN_PRE_FWD) != 0;
     if (active) {
       const float al = float(a.alpha);
 #pragma unroll
@@ -285,7 +223,25 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS) k_rows(const RowsArgs<T> 
         const float br = 1.f - vv.x, bi = -vv.y;
         const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
         acc += dr * dr + di * di;
-        if (!(a.flags & F_REF)) a.x_out[i] = make_float2(xv.x + al * dr, xv.y + al * di);
+        const float2 xn = make_float2(xv.x + al * dr, xv.y + al * di);
+        if (!(a.flags & F_REF)) a.x_out[i] = xn;
+        if (then_pre) {
+          // next iteration's B x + y, from the updated iterate
+          const float2 yv = a.y[i];
+          v[q] = mkc<V>(T(yv.x + br * xn.x - bi * xn.y), T(yv.y + br * xn.y + bi * xn.x));
+        }
+      }
+    }
+    if (then_pre) {
+      V t[N1];
+      out_to_in<N>(v, t);
+#pragma unroll
+      for (int q = 0; q < N1; ++q) v[q] = t[q];
+      fft_rows<N, false>(v, exr, tw, g);
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q)
+          reinterpret_cast<V*>(a.buf)[base + out_index<N>(g, q)] = v[q];
       }
     }
     reduce_and_finalize<THREADS>((double)acc, a.partials, a.st, a.hist, a.flags);
@@ -377,7 +333,11 @@ __global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) 
       // This pass runs on axis 0 after all faster axes were transformed, so
       // the column index decomposes into their frequency indices.
       T p2in = T(0);
-      if (a.sym.ndim == 3) {
+      if (a.flags & F_CBLOCK) {
+        // column-block layout of the fused schedule: col = (cb * 256 + ky) * 32 + xl
+        p2in = axis_p2(a.sym, 2, int((col >> 13) * 32 + (col & 31))) +
+               axis_p2(a.sym, 1, int((col >> 5) & 255));
+      } else if (a.sym.ndim == 3) {
         p2in = axis_p2(a.sym, 2, int(col % a.sym.n[2])) + axis_p2(a.sym, 1, int(col / a.sym.n[2]));
       } else if (a.sym.ndim == 2) {
         p2in = axis_p2(a.sym, 1, int(col));
@@ -494,6 +454,12 @@ static cudaError_t attrs_all() {
 
 // Twiddles from the first octant by symmetry, so W^(64 j) are exactly
 // 1, -i, -1, i and the table is exactly symmetric.
+const float2* twiddle_table_f32() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_tw32) != cudaSuccess) return nullptr;
+  return static_cast<const float2*>(p);
+}
+
 cudaError_t init_twiddles() {
   float2 h32[256];
   double2 h64[256];

@@ -7,6 +7,8 @@
 // convergence cost only empty launches; the host reads the device state
 // once per group of graph launches (the only device-to-host sync of the
 // loop).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,6 +70,8 @@ static usp_status ensure_device_init() {
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (dev < 64 && (g_init_mask >> dev) & 1ull) return USP_OK;
   CUDA_TRY(init_twiddles());
+  CUDA_TRY(plane_kernel_init());
+  CUDA_TRY(cols_tma_init());
   if (dev < 64) g_init_mask |= (1ull << dev);
   return USP_OK;
 }
@@ -114,6 +118,10 @@ struct usp_solver {
   std::vector<double> history;
   Sym<float> symf{};
   Sym<double> symd{};
+  const float2* tw32 = nullptr;    // device twiddle table (fused plane pass)
+  int num_sms = 0;
+  bool maps_ok = false;            // TMA tensor maps of the scratch field
+  CUtensorMap map_ax[2];           // [axis]: strided-axis views of s->buf (axis 0, axis 1)
 };
 
 static bool is_pow2_in_range(int64_t v) { return v >= 2 && v <= 256 && (v & (v - 1)) == 0; }
@@ -121,6 +129,50 @@ static bool is_pow2_in_range(int64_t v) { return v >= 2 && v <= 256 && (v & (v -
 static void free_graphs(usp_solver* s) {
   for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
   s->graphs.clear();
+}
+
+// ------------------------------------------------------ TMA tensor maps ---
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static bool tensor_map_encoder() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+// The field viewed as [outer][n][inner] complex64 (8-byte elements), tiles of
+// {32, n, 1}.
+static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, int64_t outer) {
+  if (!tensor_map_encoder()) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)n, (cuuint64_t)outer};
+  const cuuint64_t strides[2] = {(cuuint64_t)inner * 8, (cuuint64_t)n * inner * 8};
+  const cuuint32_t box[3] = {32, (cuuint32_t)n, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static void build_maps(usp_solver* s) {
+  s->maps_ok = false;
+  if (s->ndim < 2) return;
+  bool ok = true;
+  for (int axis = 0; axis < s->ndim - 1 && axis < 2; ++axis) {
+    int64_t inner = 1, outer = 1;
+    for (int ax = axis + 1; ax < s->ndim; ++ax) inner *= s->n[ax];
+    for (int ax = 0; ax < axis; ++ax) outer *= s->n[ax];
+    ok = ok && encode_cols_map(&s->map_ax[axis], s->buf, inner, s->n[axis], outer);
+  }
+  s->maps_ok = ok;
 }
 
 // ------------------------------------------------------ the schedule ---
@@ -157,6 +209,28 @@ static ColsArgs<T> cols_args(const usp_solver* s, int axis, int mode, int mul, i
   return c;
 }
 
+// A strided-axis FP32 pass: TMA-staged tiles when available, else plain.
+static std::function<cudaError_t(cudaStream_t)> cols_pass_f32(usp_solver* s, int axis, int mode,
+                                                              int flags) {
+  auto c = cols_args<float>(s, axis, mode, MUL_LINV, flags, s->buf, s->symf);
+  const int n = s->n[axis];
+  if (s->maps_ok && !s->opt.no_tma) {
+    ColsTmaArgs t{};
+    t.mode = mode;
+    t.mul = MUL_LINV;
+    t.flags = flags;
+    t.inner_blocks = c.inner_blocks;
+    t.tiles = c.inner_blocks * c.outer;
+    t.st = s->st;
+    t.tw = s->tw32;
+    t.sym = s->symf;
+    const int grid = (int)std::min<int64_t>(t.tiles, s->num_sms);
+    const CUtensorMap map = s->map_ax[axis];
+    return [=](cudaStream_t st) { return launch_cols_tma(n, map, t, grid, st); };
+  }
+  return [=](cudaStream_t st) { return launch_cols_f32(n, c, st); };
+}
+
 // One pass of an iteration: a kernel launch plus what it moves.
 struct PassLaunch {
   const char* name;
@@ -167,19 +241,17 @@ struct PassLaunch {
 // Kernel launches issued by this library (graph launches count their nodes).
 static std::atomic<int64_t> g_launches{0};
 
-// The passes of one FP32 iteration (or of the reference pass) on the pencil
-// schedule.  y: source; xin/xout: iterate in/out (xin unused with F_XZERO).
-static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, const float2* xin,
-                                             float2* xout, int flags) {
-  std::vector<PassLaunch> P;
-  const int vflag = s->vreal ? F_VREAL : 0;
-  const double vb = s->vreal ? 4.0 : 8.0;
-  const bool xz = (flags & F_XZERO) != 0, ref = (flags & F_REF) != 0;
-  const int nd = s->ndim;
-  const int nx = s->n[nd - 1];
+// The passes of the pencil schedule.  y: source; xin/xout: iterate in/out
+// (xin unused with F_XZERO).
+//   prologue  : rows pass t = (1-V) x + y, FFT x  (once per phase)
+//   iteration : column passes; rows pass inverse FFT x, Delta, update, norm,
+//               and (fused) the next iteration's B x + y with its FFT x.
+// A reference pass (F_REF) is prologue + columns + an unfused rows pass.
+static RowsArgs<float> rows_args(usp_solver* s, const float2* y, const float2* xin,
+                                 float2* xout, int flags) {
   RowsArgs<float> r{};
-  r.flags = flags | vflag;
-  r.nrows = s->N / nx;
+  r.flags = flags | (s->vreal ? F_VREAL : 0);
+  r.nrows = s->N / s->n[s->ndim - 1];
   r.x_in = xin;
   r.x_out = xout;
   r.y = y;
@@ -191,48 +263,139 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
   r.alpha = (float)s->alpha;
   r.sym = s->symf;
   r.mul = MUL_LINV;
+  return r;
+}
+
+static std::vector<PassLaunch> pencil_prologue(usp_solver* s, const float2* y, const float2* xin,
+                                               int flags) {
+  std::vector<PassLaunch> P;
+  if (s->ndim == 1) return P;
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0;
+  const int nx = s->n[s->ndim - 1];
   const int64_t grid = rows_grid_f32(s);
-  const double pre_bytes = 8.0 + (xz ? 0.0 : 8.0 + vb);                 // y, x, V
-  const double post_bytes = vb + (xz ? 0.0 : 8.0) + (ref ? 0.0 : 8.0);   // V, x in, x out
+  RowsArgs<float> r = rows_args(s, y, xin, nullptr, flags);
+  r.mode = R_IN_PRE | R_FWD | R_OUT_BUF;
+  P.push_back({"rows_pre_fwd", 16.0 + (xz ? 0.0 : 8.0 + vb),
+               [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
+  return P;
+}
+
+static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, const float2* xin,
+                                             float2* xout, int flags) {
+  std::vector<PassLaunch> P;
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0, ref = (flags & F_REF) != 0;
+  const int nd = s->ndim;
+  const int nx = s->n[nd - 1];
+  const int64_t grid = rows_grid_f32(s);
+  RowsArgs<float> r = rows_args(s, y, xin, xout, flags);
   if (nd == 1) {
     r.mode = R_IN_PRE | R_FWD | R_MUL | R_INV | R_OUT_POST;
-    P.push_back({"rows_full", pre_bytes + post_bytes - (xz ? 0.0 : vb + 8.0),
+    P.push_back({"rows_full", 8.0 + vb + (xz ? 0.0 : 8.0) + (ref ? 0.0 : 8.0),
                  [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
     return P;
   }
-  RowsArgs<float> r1 = r;
-  r1.mode = R_IN_PRE | R_FWD | R_OUT_BUF;
-  P.push_back({"rows_pre_fwd", pre_bytes + 8.0,
-               [=](cudaStream_t t) { return launch_rows_f32(nx, r1, grid, t); }});
   const int cflags = flags & ~F_XZERO & ~F_REF;
   if (nd == 2) {
-    auto c = cols_args<float>(s, 0, COL_FWD_MUL_INV, MUL_LINV, cflags, s->buf, s->symf);
-    const int n0 = s->n[0];
-    P.push_back({"cols0_fwd_mul_inv", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n0, c, t); }});
+    P.push_back({"cols0_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
   } else {
-    const int n0 = s->n[0], n1 = s->n[1];
-    auto c1 = cols_args<float>(s, 1, COL_FWD, MUL_LINV, cflags, s->buf, s->symf);
-    auto c0 = cols_args<float>(s, 0, COL_FWD_MUL_INV, MUL_LINV, cflags, s->buf, s->symf);
-    auto c2 = cols_args<float>(s, 1, COL_INV, MUL_LINV, cflags, s->buf, s->symf);
-    P.push_back({"cols1_fwd", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n1, c1, t); }});
-    P.push_back({"cols0_fwd_mul_inv", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n0, c0, t); }});
-    P.push_back({"cols1_inv", 16.0, [=](cudaStream_t t) { return launch_cols_f32(n1, c2, t); }});
+    P.push_back({"cols1_fwd", 16.0, cols_pass_f32(s, 1, COL_FWD, cflags)});
+    P.push_back({"cols0_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
+    P.push_back({"cols1_inv", 16.0, cols_pass_f32(s, 1, COL_INV, cflags)});
   }
-  RowsArgs<float> r2 = r;
-  r2.mode = R_IN_BUF | R_INV | R_OUT_POST;
-  P.push_back({"rows_inv_post", 8.0 + post_bytes,
-               [=](cudaStream_t t) { return launch_rows_f32(nx, r2, grid, t); }});
+  if (ref) {
+    r.mode = R_IN_BUF | R_INV | R_OUT_POST;
+    P.push_back({"rows_inv_post", 8.0 + vb,
+                 [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
+  } else {
+    // read scratch, V, x (unless zero), y; write x, scratch
+    r.mode = R_IN_BUF | R_INV | R_OUT_POST | R_THEN_PRE_FWD;
+    P.push_back({"rows_inv_post_pre_fwd", 32.0 + vb + (xz ? 0.0 : 8.0),
+                 [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
+  }
+  return P;
+}
+
+// ---- fused two-pass schedule (grids nz x 256 x 256, fused3d_kernels.cu)
+
+static bool fused_supported(const usp_solver* s) {
+  return s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256;
+}
+static bool use_fused(const usp_solver* s) {
+  if (s->opt.schedule == 1) return false;
+  return fused_supported(s);
+}
+
+static PlaneArgs plane_args(usp_solver* s, const float2* y, const float2* xin, float2* xout,
+                            int flags, int mode) {
+  PlaneArgs p{};
+  p.mode = mode;
+  p.flags = flags | (s->vreal ? F_VREAL : 0);
+  p.nz = s->n[0];
+  p.x_in = xin;
+  p.x_out = xout;
+  p.y = y;
+  p.V = s->V;
+  p.buf = s->buf;
+  p.tw = s->tw32;
+  p.partials = s->partials;
+  p.st = s->st;
+  p.hist = s->hist;
+  p.alpha = (float)s->alpha;
+  return p;
+}
+
+static std::vector<PassLaunch> fused_prologue(usp_solver* s, const float2* y, const float2* xin,
+                                              int flags) {
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0;
+  PlaneArgs p = plane_args(s, y, xin, nullptr, flags & ~F_REF, PL_PRE);
+  return {{"plane_pre", 16.0 + (xz ? 0.0 : 8.0 + vb),
+           [=](cudaStream_t t) { return launch_plane(p, t); }}};
+}
+
+static std::vector<PassLaunch> fused_passes(usp_solver* s, const float2* y, const float2* xin,
+                                            float2* xout, int flags) {
+  std::vector<PassLaunch> P;
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0, ref = (flags & F_REF) != 0;
+  const int cflags = (flags & ~F_XZERO & ~F_REF) | F_CBLOCK;
+  P.push_back({"z_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
+  if (ref) {
+    PlaneArgs p = plane_args(s, y, xin, xout, flags, PL_POST);
+    P.push_back({"plane_post", 8.0 + vb, [=](cudaStream_t t) { return launch_plane(p, t); }});
+  } else {
+    PlaneArgs p = plane_args(s, y, xin, xout, flags, PL_FULL);
+    P.push_back({"plane_full", 32.0 + vb + (xz ? 0.0 : 8.0),
+                 [=](cudaStream_t t) { return launch_plane(p, t); }});
+  }
   return P;
 }
 
 static std::vector<PassLaunch> iteration_passes(usp_solver* s, const float2* y, const float2* xin,
                                                 float2* xout, int flags) {
+  if (use_fused(s)) return fused_passes(s, y, xin, xout, flags);
   return pencil_passes(s, y, xin, xout, flags);
 }
 
+static std::vector<PassLaunch> prologue_passes(usp_solver* s, const float2* y, const float2* xin,
+                                               int flags) {
+  if (use_fused(s)) return fused_prologue(s, y, xin, flags);
+  return pencil_prologue(s, y, xin, flags);
+}
+
+// One iteration; with `first` the phase's prologue is launched before it.
 static cudaError_t enqueue_iteration(usp_solver* s, const float2* y, const float2* xin,
                                      float2* xout, int flags, cudaStream_t strm,
-                                     bool count = true) {
+                                     bool count = true, bool first = false) {
+  if (first) {
+    for (auto& p : prologue_passes(s, y, xin, flags)) {
+      cudaError_t e = p.go(strm);
+      if (e != cudaSuccess) return e;
+      if (count) g_launches.fetch_add(1);
+    }
+  }
   for (auto& p : iteration_passes(s, y, xin, xout, flags)) {
     cudaError_t e = p.go(strm);
     if (e != cudaSuccess) return e;
@@ -416,6 +579,10 @@ extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol*
   }
   s->vmax = vmax;
   s->alpha = alpha > 0.0 ? alpha : astar;
+  s->tw32 = twiddle_table_f32();
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (s->num_sms < 1) s->num_sms = 1;
+  build_maps(s);
   *out = s;
   return USP_OK;
 #undef CREATE_TRY
@@ -425,6 +592,9 @@ extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* o
   if (!s || !opt) return fail(USP_ERR_INVALID_ARG, "NULL argument");
   if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 2)
     return fail(USP_ERR_INVALID_ARG, "invalid option value");
+  if (opt->schedule == 2 && !fused_supported(s))
+    return fail(USP_ERR_UNSUPPORTED_SIZE, "the fused schedule needs a 3-D grid nz x 256 x 256");
+  free_graphs(s);  // captured graphs follow the old schedule
   s->opt = *opt;
   return USP_OK;
 }
@@ -493,7 +663,7 @@ static usp_status run_phase(usp_solver* s, const float2* y, float2* x, bool zero
   const int chunk = s->opt.chunk > 0 ? s->opt.chunk : 8;
   // the first iteration is launched directly (it may start from x = 0)
   {
-    cudaError_t e = enqueue_iteration(s, y, x, x, zero_start ? F_XZERO : 0, s->stream);
+    cudaError_t e = enqueue_iteration(s, y, x, x, zero_start ? F_XZERO : 0, s->stream, true, true);
     if (e != cudaSuccess) return fail(USP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
   }
   const int64_t passes_per_it = (int64_t)iteration_passes(s, y, x, x, 0).size();
@@ -553,7 +723,7 @@ static usp_status solve_impl(usp_solver* s, const float2* y, float2* x, int use_
   bool skip = false;
   if (use_x0 && !(ref_norm > 0)) {
     // ||B (L+I)^-1 y||: Delta at x = 0, no update (Algorithm 1's denominator)
-    cudaError_t e = enqueue_iteration(s, y, x, x, F_XZERO | F_REF, s->stream);
+    cudaError_t e = enqueue_iteration(s, y, x, x, F_XZERO | F_REF, s->stream, true, true);
     if (e != cudaSuccess) return fail(USP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     if ((st = read_state(s)) != USP_OK) return st;
     skip = h.done != 0;  // non-finite y
@@ -577,7 +747,7 @@ static usp_status solve_impl(usp_solver* s, const float2* y, float2* x, int use_
     }
     const int stt = h.status;
     stagnated = (stt == ST_STAGNATED);
-    if (stt == ST_NONFINITE || stt == ST_DIVERGED || stt == ST_MAXIT) break;
+    if (stt == ST_NONFINITE || stt == ST_DIVERGED || stt == ST_MAXIT || stt == ST_TIMEOUT) break;
     if (h.last_r < tol || h.ref == 0.0) break;  // converged
     if (!can_refine) break;
     // Refinement: Delta(x_b + z; y) = Delta(z; y - A x_b) exactly because
@@ -597,7 +767,8 @@ static usp_status solve_impl(usp_solver* s, const float2* y, float2* x, int use_
   s->history.assign(nit, 0.0);
   if (nit > 0) CUDA_TRY(cudaMemcpy(s->history.data(), s->hist, sizeof(double) * nit, cudaMemcpyDeviceToHost));
 
-  const bool converged = (h.status != ST_NONFINITE && h.status != ST_DIVERGED) &&
+  const bool converged = (h.status != ST_NONFINITE && h.status != ST_DIVERGED &&
+                          h.status != ST_TIMEOUT) &&
                          (h.it > 0 || h.ref == 0.0) && (h.last_r < tol || h.ref == 0.0);
   if (out) {
     out->iterations = h.it;
@@ -608,6 +779,7 @@ static usp_status solve_impl(usp_solver* s, const float2* y, float2* x, int use_
     out->ref_norm = h.ref;
     out->alpha = s->alpha;
   }
+  if (h.status == ST_TIMEOUT) return fail(USP_ERR_CUDA, "a bounded wait for the copy engine timed out");
   if (h.status == ST_NONFINITE) return fail(USP_ERR_NONFINITE, "non-finite value in y, x0 or an iterate");
   if (h.status == ST_DIVERGED)
     return fail(USP_ERR_DIVERGED, "||Delta|| grew from %.3g to %.3g (relative)", h.phase_first_r, h.last_r);
@@ -753,6 +925,11 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
   h.ref = 1.0;   // fixed denominator: nothing stops the timed iterations
   h.tol = 0.0;
   if ((st = write_state(s)) != USP_OK) return st;
+  for (auto& p : prologue_passes(s, (const float2*)y, (const float2*)x, 0)) {
+    cudaError_t e = p.go(s->stream);
+    if (e != cudaSuccess) return fail(USP_ERR_CUDA, "prologue: %s", cudaGetErrorString(e));
+    g_launches.fetch_add(1);
+  }
   auto passes = iteration_passes(s, (const float2*)y, (const float2*)x, (float2*)x, 0);
   const size_t np = passes.size();
   std::vector<cudaEvent_t> ev(2 * np, nullptr);

@@ -34,10 +34,11 @@ class Solver:
     alpha : step size; <= 0 selects Re[B^-1] = min Re 1/(1 - V).
     plain : True runs Algorithm 1 exactly (no FP64 refinement).
     schedule : 0 auto, 1 pencil passes, 2 fused two-pass 3-D schedule.
+    no_tma : True loads the strided-axis passes with plain global accesses.
     """
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
-                 schedule=0, chunk=0, max_refinements=0):
+                 schedule=0, chunk=0, max_refinements=0, no_tma=False):
         import torch
         L = _lib.lib()
         if not V.is_cuda:
@@ -65,10 +66,11 @@ class Solver:
                                       ctypes.c_void_p(stream), ctypes.byref(h)))
         self._h = h
         self.set_options(plain=plain, schedule=schedule, chunk=chunk,
-                         max_refinements=max_refinements)
+                         max_refinements=max_refinements, no_tma=no_tma)
 
-    def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0):
-        o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements))
+    def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False):
+        o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements),
+                    int(bool(no_tma)))
         check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
 
     @property

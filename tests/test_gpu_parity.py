@@ -60,9 +60,9 @@ def _oracle_iterate(shape, cf, V, y, n_iter, alpha):
     return uo.iterate(V.astype(np.complex128), y.astype(np.complex128), Lh, alpha, n_iter)
 
 
-def _check_trajectory(torch, shape, prob, n_iter, vreal=False, alpha=0.0):
+def _check_trajectory(torch, shape, prob, n_iter, vreal=False, alpha=0.0, schedule=0):
     cf, V, y = _prep(prob, vreal)
-    xg, res, hg = _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha)
+    xg, res, hg = _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha, schedule)
     assert res["iterations"] == n_iter
     a = res["alpha"]
     if alpha <= 0:
@@ -121,6 +121,58 @@ def test_parity_fixed_alpha(torch_cuda):
     prob = inputs.random_helmholtz((32, 64), 6, sigma_px=2.0)
     for alpha in (1.0, 0.7):
         _check_trajectory(torch_cuda, (32, 64), prob, 40, alpha=alpha)
+
+
+# ----------------------------------------- fused two-pass schedule ---
+
+@pytest.mark.parametrize("nz", [2, 16])
+def test_parity_fused_schedule(torch_cuda, nz):
+    """Grids nz x 256 x 256 on the plane-cluster + z-pencil schedule."""
+    shape = (nz, 256, 256)
+    _check_trajectory(torch_cuda, shape, inputs.white_helmholtz(shape, 30 + nz), 20, schedule=2)
+
+
+def test_parity_fused_real_potential(torch_cuda):
+    shape = (8, 256, 256)
+    prob = inputs.random_diffusion(shape, 33, sigma_px=3.0)
+    _check_trajectory(torch_cuda, shape, prob, 20, vreal=True, schedule=2)
+
+
+def test_fused_and_pencil_schedules_agree(torch_cuda):
+    """Both schedules compute the same iteration; they differ only in the
+    order of FP32 rounding."""
+    torch = torch_cuda
+    shape = (32, 256, 256)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 34, sigma_px=3.0, abl_width=4))
+    x1, r1, h1 = _gpu_iterate(torch, shape, cf, V, y, 50, schedule=1)
+    x2, r2, h2 = _gpu_iterate(torch, shape, cf, V, y, 50, schedule=2)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 2e-6
+    assert np.max(np.abs(h1 - h2) / h1) < 1e-5
+
+
+def test_fused_warm_start_and_reference_pass(torch_cuda):
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (4, 256, 256)
+    cf, V, y = _prep(inputs.white_helmholtz(shape, 35))
+    dev = torch.device("cuda:0")
+    yd = torch.from_numpy(y).to(dev)
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), plain=True,
+                schedule=2) as s:
+        x, r1 = s.solve(yd, tol=0.0, maxit=15)
+        x, r2 = s.solve(yd, x=x, use_x0=True, tol=0.0, maxit=15)   # reference pass
+    assert r2["ref_norm"] == pytest.approx(r1["ref_norm"], rel=1e-5)
+    xo, _ = _oracle_iterate(shape, cf, V, y, 30, r1["alpha"])
+    assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= TOL_X
+
+
+def test_parity_full_size_256_bench_configuration(torch_cuda):
+    """The benchmark's workload (3-D Helmholtz 256^3) in the benchmark's
+    launch configuration (automatic schedule), every output compared with
+    the oracle after 3 iterations."""
+    shape = (256, 256, 256)
+    prob = inputs.helmholtz_3d(256, seed=0)
+    _check_trajectory(torch_cuda, shape, prob, 3)
 
 
 # ------------------------------------------------------ full solves ---
