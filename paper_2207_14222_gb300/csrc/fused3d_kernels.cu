@@ -23,6 +23,7 @@
 #include "fft_core.cuh"
 #include "iteration_state.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -35,6 +36,9 @@ constexpr int PC = 8;              // CTAs per plane (cluster size)
 constexpr int PR = PN / PC;        // rows / columns per CTA
 constexpr int PTHREADS = 512;      // 16 warps
 constexpr size_t PSMEM = sizeof(float2) * (PN + PR * PN);
+// staged variant: + V rows (complex64 worst case) + y rows
+constexpr size_t PSMEM_TMA = sizeof(float2) * (PN + 3 * PR * PN);
+constexpr uint32_t CHUNK_BYTES = sizeof(float2) * PR * PN;   // 64 KB
 
 __device__ __forceinline__ double block_sum512(double v, double* red) {
 #pragma unroll
@@ -97,13 +101,23 @@ __device__ __forceinline__ float2 ld_v(const void* V, int64_t i, bool vreal) {
 }
 
 // One xy-plane per cluster; cluster rank r owns rows / column block r.
-__global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
+// STAGED: the scratch column block, V rows and y rows arrive by bulk copies
+// issued at CTA start (the column block straight into the exchange buffer),
+// and x is prefetched into registers, so all inputs are in flight before
+// the first transform.  Bounded waits; a CTA whose wait times out still
+// takes every cluster barrier so its siblings cannot hang.
+template <bool STAGED>
+__global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, STAGED ? 1 : 2)
     k_plane(const PlaneArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* B = tw + PN;  // 32 x 256 complex: exchange and transpose buffer
+  float2* B = tw + PN;          // 32 x 256 complex: exchange and transpose buffer
+  float2* SV = B + PR * PN;     // staged V rows (STAGED)
+  float2* SY = SV + PR * PN;    // staged y rows (STAGED)
   __shared__ double red[PTHREADS / 32];
   __shared__ int is_last;
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int ok_flag;
 
   if (!(a.flags & F_NOSTATE) && a.st->done) return;
 
@@ -117,19 +131,64 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
   const bool vreal = (a.flags & F_VREAL) != 0;
   const bool do_post = a.mode != PL_PRE;
   const bool do_pre = a.mode != PL_POST;
+  const int64_t cblk = (z * PC + r) * (int64_t)(PN * PR);      // this CTA's column block
+  const int64_t rows0 = z * (int64_t)(PN * PN) + (int64_t)(PR * r) * PN;  // its first row
+  const int64_t row0 = rows0 + (int64_t)rho * PN;               // this thread's row
+  bool ok = true;
+
+  if (STAGED && tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
   for (int m = tid; m < PN; m += PTHREADS) tw[m] = a.tw[m];
   __syncthreads();
+  if (STAGED && tid == 0) {
+    if (do_post) {
+      mbar_arrive_expect_tx(&bars[0], CHUNK_BYTES);
+      bulk_load(B, a.buf + cblk, CHUNK_BYTES, &bars[0]);
+    }
+    const uint32_t vbytes = vreal ? CHUNK_BYTES / 2 : CHUNK_BYTES;
+    const bool need_v = do_post || !xzero;
+    const bool need_y = do_pre;
+    mbar_arrive_expect_tx(&bars[1], (need_v ? vbytes : 0u) + (need_y ? CHUNK_BYTES : 0u));
+    if (need_v) {
+      const void* vsrc = vreal ? (const void*)(reinterpret_cast<const float*>(a.V) + rows0)
+                               : (const void*)(reinterpret_cast<const float2*>(a.V) + rows0);
+      bulk_load(SV, vsrc, vbytes, &bars[1]);
+    }
+    if (need_y) bulk_load(SY, a.y + rows0, CHUNK_BYTES, &bars[1]);
+  }
+  auto wait_bar = [&](int i) {   // uniform outcome for the whole CTA
+    if (tid == 0) ok_flag = mbar_wait(&bars[i], 0) ? 1 : 0;
+    __syncthreads();
+    ok = ok && ok_flag;
+  };
+  // V, y of this thread's point x (row layout)
+  auto vval = [&](int x) -> float2 {
+    if (STAGED) return vreal ? make_float2(reinterpret_cast<const float*>(SV)[rho * PN + x], 0.f)
+                             : SV[rho * PN + x];
+    return ld_v(a.V, row0 + x, vreal);
+  };
+  auto yval = [&](int x) -> float2 { return STAGED ? SY[rho * PN + x] : a.y[row0 + x]; };
 
-  const int64_t cblk = (z * PC + r) * (int64_t)(PN * PR);     // this CTA's column block
-  const int64_t row0 = z * (int64_t)(PN * PN) + (int64_t)(PR * r + rho) * PN;  // its row
   float2* exr = B + rho * PN;
   float2 v[16];
   float acc = 0.f;
 
   if (do_post) {
+    float2 xr[16];
+    if (STAGED) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        xr[q] = xzero ? make_float2(0.f, 0.f) : a.x_in[row0 + g + 16 * q];
+      wait_bar(0);
+    }
     // ---- inverse FFT along y on this CTA's 32 columns
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = a.buf[cblk + (16 * q + w) * PR + l];
+    for (int q = 0; q < 16; ++q)
+      v[q] = STAGED ? B[(16 * q + w) * PR + l] : a.buf[cblk + (16 * q + w) * PR + l];
+    if (STAGED) __syncthreads();    // B becomes the exchange buffer
     fft_cols_x<PN, true>(v, B, tw, w, l);
 #pragma unroll
     for (int q = 0; q < 16; ++q) B[(w + 16 * q) * PR + l] = v[q];   // B[y][xl]
@@ -143,12 +202,14 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
     cluster.sync();
     // ---- inverse FFT along x; Delta, update, next B x + y
     fft_rows_x<PN, true>(v, exr, tw, g);
+    if (STAGED) wait_bar(1);
     const float al = a.alpha;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int64_t i = row0 + g + 16 * q;
-      const float2 vv = ld_v(a.V, i, vreal);
-      const float2 xv = xzero ? make_float2(0.f, 0.f) : a.x_in[i];
+      const int x = g + 16 * q;
+      const int64_t i = row0 + x;
+      const float2 vv = vval(x);
+      const float2 xv = STAGED ? xr[q] : (xzero ? make_float2(0.f, 0.f) : a.x_in[i]);
       const float ur = v[q].x - xv.x, ui = v[q].y - xv.y;
       const float br = 1.f - vv.x, bi = -vv.y;
       const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
@@ -156,23 +217,26 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
       const float2 xn = make_float2(xv.x + al * dr, xv.y + al * di);
       if (!(a.flags & F_REF)) a.x_out[i] = xn;
       if (do_pre) {
-        const float2 yv = a.y[i];
+        const float2 yv = yval(x);
         v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
       }
     }
   } else {
     // prologue: t = (1-V) x + y at x = 16 q + g
+    float2 xr[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      xr[q] = xzero ? make_float2(0.f, 0.f) : a.x_in[row0 + 16 * q + g];
+    if (STAGED) wait_bar(1);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int64_t i = row0 + 16 * q + g;
-      const float2 yv = a.y[i];
-      float2 t = yv;
+      const int x = 16 * q + g;
+      float2 t = yval(x);
       if (!xzero) {
-        const float2 vv = ld_v(a.V, i, vreal);
-        const float2 xv = a.x_in[i];
+        const float2 vv = vval(x);
         const float br = 1.f - vv.x, bi = -vv.y;
-        t.x += br * xv.x - bi * xv.y;
-        t.y += br * xv.y + bi * xv.x;
+        t.x += br * xr[q].x - bi * xr[q].y;
+        t.y += br * xr[q].y + bi * xr[q].x;
       }
       v[q] = t;
     }
@@ -197,6 +261,14 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
     for (int q = 0; q < 16; ++q) a.buf[cblk + (w + 16 * q) * PR + l] = v[q];
   }
 
+  if (STAGED && !ok && tid == 0) {
+    // let late copies land before this CTA's shared memory is released
+    if (do_post) mbar_wait(&bars[0], 0);
+    mbar_wait(&bars[1], 0);
+    a.st->status = ST_TIMEOUT;
+    a.st->done = 1;
+  }
+
   if (do_post) {
     const double bs = block_sum512((double)acc, red);
     if (threadIdx.x == 0) {
@@ -212,7 +284,7 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
       for (unsigned i = threadIdx.x; i < gridDim.x; i += PTHREADS) s += __ldcg(a.partials + i);
       const double tot = block_sum512(s, red);
       if (threadIdx.x == 0) {
-        finalize_iteration(a.st, a.hist, tot, a.flags);
+        if (a.st->status != ST_TIMEOUT) finalize_iteration(a.st, a.hist, tot, a.flags);
         a.st->ticket = 0u;
       }
     }
@@ -220,11 +292,18 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 2)
 }
 
 cudaError_t plane_kernel_init() {
-  return cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PSMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PSMEM_TMA);
 }
 
 cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
-  k_plane<<<(unsigned)(a.nz * PC), PTHREADS, PSMEM, s>>>(a);
+  if (a.staged)
+    k_plane<true><<<(unsigned)(a.nz * PC), PTHREADS, PSMEM_TMA, s>>>(a);
+  else
+    k_plane<false><<<(unsigned)(a.nz * PC), PTHREADS, PSMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -232,7 +311,7 @@ int plane_max_active_clusters() {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(PC * 256, 1, 1);
   cfg.blockDim = dim3(PTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = PSMEM;
+  cfg.dynamicSmemBytes = PSMEM_TMA;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
   attr.val.clusterDim.x = PC;
@@ -241,7 +320,7 @@ int plane_max_active_clusters() {
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_plane, &cfg) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveClusters(&n, k_plane<true>, &cfg) != cudaSuccess) return -1;
   return n;
 }
 

@@ -140,6 +140,7 @@ struct PlaneArgs {
   DevState* st;
   double* hist;
   float alpha;
+  int staged;           // inputs by bulk copy (all pointers 16-byte aligned)
 };
 
 cudaError_t plane_kernel_init();

@@ -48,7 +48,8 @@ __device__ __forceinline__ float2 spectral_factor_f(float p2, const Sym<float>& 
   const float li = s.a_im * p2 + s.b_im;
   if (mul == MUL_L) return make_float2(lr * s.inv_n, li * s.inv_n);
   const float dr = lr + 1.f;
-  const float sc = s.inv_n / (dr * dr + li * li);
+  // fast reciprocal division (about 2 ulp); the denominator |Lhat + 1|^2 >= 1
+  const float sc = __fdividef(s.inv_n, dr * dr + li * li);
   return make_float2(dr * sc, -li * sc);
 }
 
