@@ -128,15 +128,21 @@ struct Split {
   static_assert(N1 * N2 == N && N2 <= N1 && N1 <= 16, "unsupported FFT size");
 };
 
+// Stage-1 twiddle table layout: tw[k1 * N2 + g] = W_N^(g k1) (k1 < N1,
+// g < N2), so that the threads g of one transform read consecutive entries
+// (no shared-memory bank conflicts) and a warp sharing g reads one entry.
+__host__ __device__ __forceinline__ int stage1_twiddle_exponent(int m, int N2) {
+  return (m % N2) * (m / N2);
+}
+
 // Stage 1: in-register DFT_N1, then v[k1] *= W_N^(g k1) (conjugate if INV).
-// tw[m] = W_N^m, m in [0, N).
 template <int N, bool INV, typename V>
 __device__ __forceinline__ void stage1(V* v, int g, const V* tw) {
-  constexpr int N1 = Split<N>::N1;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   DFT<N1, INV, V>::run(v);
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) {
-    const V w = tw[g * k1];
+    const V w = tw[k1 * N2 + g];
     v[k1] = INV ? cmulc(v[k1], w) : cmul(v[k1], w);
   }
 }

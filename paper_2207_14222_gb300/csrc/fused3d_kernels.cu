@@ -141,7 +141,7 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, STAGED ? 
     mbar_init(&bars[1], 1);
     fence_mbar_init();
   }
-  for (int m = tid; m < PN; m += PTHREADS) tw[m] = a.tw[m];
+  for (int m = tid; m < PN; m += PTHREADS) tw[m] = a.tw[stage1_twiddle_exponent(m, 16)];
   __syncthreads();
   if (STAGED && tid == 0) {
     if (do_post) {

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
   const int64_t base = row * N;
   const bool xzero = (a.flags & F_XZERO) != 0;
   const bool vreal = (a.flags & F_VREAL) != 0;
-  for (int m = tid; m < N; m += THREADS) tw[m] = tw_entry<T>(m * (256 / N));
+  for (int m = tid; m < N; m += THREADS) tw[m] = tw_entry<T>(stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N));
   __syncthreads();
   V* exr = ex + f * N;
 
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) 
   const bool active = col < a.inner;
   const int64_t base = o * (int64_t)N * a.inner + col;
   V* buf = reinterpret_cast<V*>(a.buf);
-  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = tw_entry<T>(m * (256 / N));
+  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = tw_entry<T>(stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N));
   __syncthreads();
 
   V v[N1];

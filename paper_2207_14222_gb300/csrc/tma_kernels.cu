@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int64_t t0 = blockIdx.x, stride = gridDim.x;
   const int64_t my = t0 < a.tiles ? (a.tiles - t0 + stride - 1) / stride : 0;
-  for (int m = threadIdx.x; m < N; m += THREADS) tw[m] = a.tw[m * (256 / N)];
+  for (int m = threadIdx.x; m < N; m += THREADS)
+    tw[m] = a.tw[stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N)];
   if (threadIdx.x == 0) {
     for (int s = 0; s < SLOTS; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
