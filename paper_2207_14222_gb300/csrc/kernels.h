@@ -164,6 +164,25 @@ cudaError_t cols_tma_init();
 cudaError_t launch_cols_tma(int n, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
                             cudaStream_t s);
 
+// Fused rows pass of the pencil schedule as a persistent, bulk-copy staged
+// kernel (tma_kernels.cu); row lengths 128 and 256.
+struct RowsTmaArgs {
+  int flags;            // F_XZERO, F_VREAL
+  int64_t nrows;
+  const float2* x_in;
+  float2* x_out;
+  const float2* y;
+  const void* V;
+  float2* buf;
+  const float2* tw;     // W_256^m table (device)
+  double* partials;     // one double per CTA
+  DevState* st;
+  double* hist;
+  float alpha;
+};
+cudaError_t rows_tma_init();
+cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s);
+
 // Launchers (pencil_kernels.cu).  n = transform length (power of two, 2..256).
 cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaStream_t s);
 cudaError_t launch_rows_f64(int n, const RowsArgs<double>& a, int64_t grid, cudaStream_t s);

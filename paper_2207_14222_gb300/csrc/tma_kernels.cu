@@ -13,6 +13,7 @@
 // of the pencil schedule and the z pass of the fused schedule (Eq.
 // laplacian_inverse: forward FFT, multiply by 1/(N (Lhat+1)), inverse FFT).
 #include "fft_core.cuh"
+#include "iteration_state.cuh"
 #include "kernels.h"
 #include "tma.cuh"
 
@@ -169,6 +170,233 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
       a.st->status = ST_TIMEOUT;
       a.st->done = 1;
     }
+  }
+}
+
+// ---------------------------------------------------------------- rows ---
+//
+// The fused rows pass of an iteration (inverse FFT x, Delta, update, ||Delta||^2,
+// next B x + y, forward FFT x) as a persistent kernel: one 512-thread CTA per
+// SM walks tiles of F = 512/G rows with three shared-memory slots of one tile
+// each, all filled by bulk copies:
+//   U slot: scratch rows; exchange buffer of the inverse transform, after
+//           which it is refilled with the next tile's rows;
+//   V slot: potential; refilled after the pointwise step;
+//   Y slot: source; exchange buffer of the forward transform (after the
+//           pointwise step consumed it), refilled at the end of the tile.
+// x of the next tile is loaded into registers right after the pointwise
+// step, so its latency overlaps the forward transform and the stores.
+
+template <int N, bool INV>
+__device__ __forceinline__ void fft_rows_slot(float2* v, float2* exr, const float2* tw, int g) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
+  stage1<N, INV>(v, g, tw);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) exr[k1 * N2 + (g ^ (k1 & (N2 - 1)))] = v[k1];
+  __syncthreads();
+  float2 w[N1];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int k1 = g + G * s;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = exr[k1 * N2 + (n2 ^ (k1 & (N2 - 1)))];
+  }
+  __syncthreads();
+  stage2<N, INV>(w);
+#pragma unroll
+  for (int q = 0; q < N1; ++q) v[q] = w[q];
+}
+
+template <int N>
+__global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
+  constexpr int N1 = Split<N>::N1, G = Split<N>::G;
+  constexpr int F = 512 / G;            // rows per tile
+  constexpr int TILE = F * N;           // complex values per tile
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* SU = reinterpret_cast<float2*>(smem_raw);
+  float2* SV = SU + TILE;
+  float2* SY = SV + TILE;
+  float2* tw = SY + TILE;
+  __shared__ __align__(8) uint64_t bars[3];   // U, V, Y slots
+  __shared__ double red[16];
+  __shared__ int is_last, ok_flag;
+
+  if (a.st->done) return;
+
+  const int tid = threadIdx.x, f = tid / G, g = tid % G;
+  const bool xzero = (a.flags & F_XZERO) != 0;
+  const bool vreal = (a.flags & F_VREAL) != 0;
+  const int64_t tiles = (a.nrows + F - 1) / F;
+  const int64_t t0 = blockIdx.x, stride = gridDim.x;
+  const int64_t my = t0 < tiles ? (tiles - t0 + stride - 1) / stride : 0;
+  bool ok = true;
+
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  for (int m = tid; m < N; m += 512)
+    tw[m] = a.tw[stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N)];
+  __syncthreads();
+
+  auto first_row = [&](int64_t k) { return (t0 + k * stride) * F; };
+  auto rows_in = [&](int64_t k) -> int64_t {   // valid rows of this CTA's k-th tile
+    const int64_t r0 = first_row(k);
+    return a.nrows - r0 < F ? a.nrows - r0 : F;
+  };
+  auto issue = [&](int which, int64_t k) {    // 0: U rows, 1: V, 2: y
+    const int64_t off = first_row(k) * N;
+    const int64_t n = rows_in(k) * N;
+    const bool real = which == 1 && vreal;
+    const uint32_t bytes = uint32_t(n * (real ? sizeof(float) : sizeof(float2)));
+    const void* src;
+    if (which == 0) src = a.buf + off;
+    else if (which == 2) src = a.y + off;
+    else src = real ? (const void*)(reinterpret_cast<const float*>(a.V) + off)
+                    : (const void*)(reinterpret_cast<const float2*>(a.V) + off);
+    float2* dst = which == 0 ? SU : (which == 1 ? SV : SY);
+    mbar_arrive_expect_tx(&bars[which], bytes);
+    bulk_load(dst, src, bytes, &bars[which]);
+  };
+  auto wait_bar = [&](int i, uint32_t parity) {
+    if (tid == 0) ok_flag = mbar_wait(&bars[i], parity) ? 1 : 0;
+    __syncthreads();
+    ok = ok && ok_flag;
+  };
+  auto release_then = [&](int which, int64_t k) {   // slot free -> refill for tile k
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && k < my) issue(which, k);
+  };
+
+  float2 xr[N1];
+  auto prefetch_x = [&](int64_t k) {    // this thread's x at points out_index(g, q)
+    const int64_t row = first_row(k) + f;
+    const bool act = row < a.nrows && !xzero;
+#pragma unroll
+    for (int q = 0; q < N1; ++q)
+      xr[q] = act ? a.x_in[row * N + out_index<N>(g, q)] : make_float2(0.f, 0.f);
+  };
+
+  if (tid == 0 && my > 0) {
+    issue(0, 0);
+    issue(1, 0);
+    issue(2, 0);
+  }
+  if (my > 0) prefetch_x(0);
+
+  float acc = 0.f;
+  for (int64_t k = 0; k < my; ++k) {
+    const uint32_t par = uint32_t(k & 1);
+    const int64_t row = first_row(k) + f;
+    const bool act = row < a.nrows;
+    wait_bar(0, par);
+    float2 v[N1];
+#pragma unroll
+    for (int q = 0; q < N1; ++q)
+      v[q] = act ? SU[f * N + in_index<N>(g, q)] : make_float2(0.f, 0.f);
+    __syncthreads();
+    // inverse FFT along x, exchange in the U slot, which is then refilled
+    fft_rows_slot<N, true>(v, SU + f * N, tw, g);
+    release_then(0, k + 1);
+    wait_bar(1, par);
+    wait_bar(2, par);
+    // Delta = (1-V)(u - x); x += alpha Delta; next t = (1-V) x + y
+    const float al = a.alpha;
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int c = f * N + out_index<N>(g, q);
+      const float2 vv = vreal ? make_float2(reinterpret_cast<const float*>(SV)[c], 0.f) : SV[c];
+      const float2 yv = SY[c];
+      const float br = 1.f - vv.x, bi = -vv.y;
+      const float ur = v[q].x - xr[q].x, ui = v[q].y - xr[q].y;
+      const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
+      const float2 xn = make_float2(xr[q].x + al * dr, xr[q].y + al * di);
+      if (act) {
+        acc += dr * dr + di * di;
+        a.x_out[row * N + out_index<N>(g, q)] = xn;
+      }
+      v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
+    }
+    release_then(1, k + 1);
+    if (k + 1 < my) prefetch_x(k + 1);
+    // forward FFT along x, exchange in the Y slot (consumed), which is then
+    // refilled; the output index set equals the input set, so the registers
+    // are reordered once into the stage-1 order
+    float2 t[N1];
+    out_to_in<N>(v, t);
+#pragma unroll
+    for (int q = 0; q < N1; ++q) v[q] = t[q];
+    fft_rows_slot<N, false>(v, SY + f * N, tw, g);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < N1; ++q) a.buf[row * N + out_index<N>(g, q)] = v[q];
+    }
+    release_then(2, k + 1);
+  }
+
+  if (!ok && tid == 0) {
+    a.st->status = ST_TIMEOUT;
+    a.st->done = 1;
+  }
+  // ||Delta||^2: block partial, the last block finalises (fixed order)
+  double dv = (double)acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dv += __shfl_down_sync(0xffffffffu, dv, o);
+  if ((tid & 31) == 0) red[tid >> 5] = dv;
+  __syncthreads();
+  if (tid == 0) {
+    double bs = 0.0;
+    for (int i = 0; i < 16; ++i) bs += red[i];
+    a.partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned tk = atomicAdd(&a.st->ticket, 1u);
+    is_last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    double sm = 0.0;
+    for (unsigned i = tid; i < gridDim.x; i += 512) sm += __ldcg(a.partials + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sm += __shfl_down_sync(0xffffffffu, sm, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = sm;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < 16; ++i) tot += red[i];
+      if (a.st->status != ST_TIMEOUT) finalize_iteration(a.st, a.hist, tot, a.flags);
+      a.st->ticket = 0u;
+    }
+  }
+}
+
+template <int N>
+static size_t rows_tma_smem() {
+  constexpr int F = 512 / Split<N>::G;
+  return sizeof(float2) * (3 * F * N + N);
+}
+
+template <int N>
+static cudaError_t rows_tma_go(const RowsTmaArgs& a, int grid, cudaStream_t s) {
+  k_rows_tma<N><<<grid, 512, rows_tma_smem<N>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t rows_tma_init() {
+  cudaError_t e = cudaFuncSetAttribute(k_rows_tma<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)rows_tma_smem<256>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rows_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rows_tma_smem<128>());
+}
+
+cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s) {
+  switch (n) {
+    case 256: return rows_tma_go<256>(a, grid, s);
+    case 128: return rows_tma_go<128>(a, grid, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

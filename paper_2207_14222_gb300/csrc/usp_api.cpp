@@ -72,6 +72,7 @@ static usp_status ensure_device_init() {
   CUDA_TRY(init_twiddles());
   CUDA_TRY(plane_kernel_init());
   CUDA_TRY(cols_tma_init());
+  CUDA_TRY(rows_tma_init());
   if (dev < 64) g_init_mask |= (1ull << dev);
   return USP_OK;
 }
@@ -310,9 +311,32 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
                  [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
   } else {
     // read scratch, V, x (unless zero), y; write x, scratch
-    r.mode = R_IN_BUF | R_INV | R_OUT_POST | R_THEN_PRE_FWD;
-    P.push_back({"rows_inv_post_pre_fwd", 32.0 + vb + (xz ? 0.0 : 8.0),
-                 [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
+    const double bytes = 32.0 + vb + (xz ? 0.0 : 8.0);
+    // bulk copies read y, V and the scratch field: 16-byte aligned sources
+    const bool aligned = (((uintptr_t)y | (uintptr_t)s->V | (uintptr_t)s->buf) & 15u) == 0;
+    if (!s->opt.no_tma && aligned && (nx == 128 || nx == 256)) {
+      RowsTmaArgs t{};
+      t.flags = r.flags;
+      t.nrows = r.nrows;
+      t.x_in = xin;
+      t.x_out = xout;
+      t.y = y;
+      t.V = s->V;
+      t.buf = s->buf;
+      t.tw = s->tw32;
+      t.partials = s->partials;
+      t.st = s->st;
+      t.hist = s->hist;
+      t.alpha = (float)s->alpha;
+      const int64_t tiles = (r.nrows + (nx == 256 ? 32 : 64) - 1) / (nx == 256 ? 32 : 64);
+      const int tgrid = (int)std::min<int64_t>(tiles, s->num_sms);
+      P.push_back({"rows_inv_post_pre_fwd", bytes,
+                   [=](cudaStream_t st) { return launch_rows_tma(nx, t, tgrid, st); }});
+    } else {
+      r.mode = R_IN_BUF | R_INV | R_OUT_POST | R_THEN_PRE_FWD;
+      P.push_back({"rows_inv_post_pre_fwd", bytes,
+                   [=](cudaStream_t t) { return launch_rows_f32(nx, r, grid, t); }});
+    }
   }
   return P;
 }
