@@ -2,7 +2,7 @@
 // (paper Algorithm 1, forward-eliminated operator of Sec. 2.1) for grids
 // nz x 256 x 256:
 //
-//   plane pass (one 8-CTA thread-block cluster per xy-plane):
+//   plane pass (8-CTA thread-block clusters, persistent over xy-planes):
 //       u = F_xy^-1 U ; Delta = (1-V)(u - x) ; x += alpha Delta ; ||Delta||^2 ;
 //       t = (1-V) x + y ; T = F_xy t                      [a5 (xy), a6-a8, a2, a3 (xy)]
 //   z pass (k_cols on the z axis):
@@ -35,10 +35,9 @@ constexpr int PN = 256;            // plane side (ny = nx)
 constexpr int PC = 8;              // CTAs per plane (cluster size)
 constexpr int PR = PN / PC;        // rows / columns per CTA
 constexpr int PTHREADS = 512;      // 16 warps
-constexpr size_t PSMEM = sizeof(float2) * (PN + PR * PN);
-// staged variant: + V rows (complex64 worst case) + y rows
-constexpr size_t PSMEM_TMA = sizeof(float2) * (PN + 3 * PR * PN);
-constexpr uint32_t CHUNK_BYTES = sizeof(float2) * PR * PN;   // 64 KB
+constexpr int CHUNK = PR * PN;     // complex values a CTA owns per plane
+constexpr uint32_t CHUNK_BYTES = sizeof(float2) * CHUNK;     // 64 KB
+constexpr size_t PSMEM = sizeof(float2) * (3 * CHUNK + PN);  // C, SV, SY, twiddles
 
 __device__ __forceinline__ double block_sum512(double v, double* red) {
 #pragma unroll
@@ -100,30 +99,38 @@ __device__ __forceinline__ float2 ld_v(const void* V, int64_t i, bool vreal) {
   return __ldg(reinterpret_cast<const float2*>(V) + i);
 }
 
-// One xy-plane per cluster; cluster rank r owns rows / column block r.
-// STAGED: the scratch column block, V rows and y rows arrive by bulk copies
-// issued at CTA start (the column block straight into the exchange buffer),
-// and x is prefetched into registers, so all inputs are in flight before
-// the first transform.  Bounded waits; a CTA whose wait times out still
-// takes every cluster barrier so its siblings cannot hang.
-template <bool STAGED>
-__global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, STAGED ? 1 : 2)
+// Persistent: cluster c processes planes c, c + nclusters, ...  CTA rank r
+// owns column block r (columns 32r..32r+31) in the column phases and rows
+// 32r..32r+31 in the row phase.  Three 64 KB slots, all filled by bulk
+// copies issued during the previous plane:
+//   C : scratch column block; exchange of the inverse FFT y; transpose source
+//       (column results); exchange of the inverse FFT x; refilled with the
+//       next plane's column block right after that.
+//   SV: V rows; exchange of the forward FFT y; refilled after it.
+//   SY: y rows; exchange of the forward FFT x; transpose source (row
+//       results); refilled after the peers have read it.
+// x of the next plane is prefetched into registers after the pointwise step.
+// Per plane: cluster barriers after each transpose source is written and
+// after the peers have read it (4 for an iteration, 2 for the prologue and
+// the reference pass).  Waits are bounded; a CTA whose wait timed out still
+// takes every barrier, so its peers cannot hang.
+__global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, 1)
     k_plane(const PlaneArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* B = tw + PN;          // 32 x 256 complex: exchange and transpose buffer
-  float2* SV = B + PR * PN;     // staged V rows (STAGED)
-  float2* SY = SV + PR * PN;    // staged y rows (STAGED)
+  float2* C = reinterpret_cast<float2*>(smem_raw);
+  float2* SV = C + CHUNK;
+  float2* SY = SV + CHUNK;
+  float2* tw = SY + CHUNK;
   __shared__ double red[PTHREADS / 32];
   __shared__ int is_last;
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[3];   // C (U column block), SV, SY
   __shared__ int ok_flag;
 
   if (!(a.flags & F_NOSTATE) && a.st->done) return;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
-  const int64_t z = blockIdx.x / PC;
+  const int ncl = gridDim.x / PC, cid = blockIdx.x / PC;
   const int tid = threadIdx.x;
   const int w = tid >> 5, l = tid & 31;      // column layout: warp = stage index, lane = column
   const int rho = tid >> 4, g = tid & 15;    // row layout: 16 threads per row
@@ -131,140 +138,142 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, STAGED ? 
   const bool vreal = (a.flags & F_VREAL) != 0;
   const bool do_post = a.mode != PL_PRE;
   const bool do_pre = a.mode != PL_POST;
-  const int64_t cblk = (z * PC + r) * (int64_t)(PN * PR);      // this CTA's column block
-  const int64_t rows0 = z * (int64_t)(PN * PN) + (int64_t)(PR * r) * PN;  // its first row
-  const int64_t row0 = rows0 + (int64_t)rho * PN;               // this thread's row
+  const bool need_v = do_post || !xzero;
   bool ok = true;
 
-  if (STAGED && tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
   }
   for (int m = tid; m < PN; m += PTHREADS) tw[m] = a.tw[stage1_twiddle_exponent(m, 16)];
   __syncthreads();
-  if (STAGED && tid == 0) {
-    if (do_post) {
+
+  auto issue = [&](int which, int64_t zz) {   // 0: U column block, 1: V rows, 2: y rows
+    const int64_t rows0 = zz * (int64_t)(PN * PN) + (int64_t)(PR * r) * PN;
+    if (which == 0) {
       mbar_arrive_expect_tx(&bars[0], CHUNK_BYTES);
-      bulk_load(B, a.buf + cblk, CHUNK_BYTES, &bars[0]);
+      bulk_load(C, a.buf + (zz * PC + r) * (int64_t)CHUNK, CHUNK_BYTES, &bars[0]);
+    } else if (which == 1) {
+      const uint32_t bytes = vreal ? CHUNK_BYTES / 2 : CHUNK_BYTES;
+      const void* src = vreal ? (const void*)(reinterpret_cast<const float*>(a.V) + rows0)
+                              : (const void*)(reinterpret_cast<const float2*>(a.V) + rows0);
+      mbar_arrive_expect_tx(&bars[1], bytes);
+      bulk_load(SV, src, bytes, &bars[1]);
+    } else {
+      mbar_arrive_expect_tx(&bars[2], CHUNK_BYTES);
+      bulk_load(SY, a.y + rows0, CHUNK_BYTES, &bars[2]);
     }
-    const uint32_t vbytes = vreal ? CHUNK_BYTES / 2 : CHUNK_BYTES;
-    const bool need_v = do_post || !xzero;
-    const bool need_y = do_pre;
-    mbar_arrive_expect_tx(&bars[1], (need_v ? vbytes : 0u) + (need_y ? CHUNK_BYTES : 0u));
-    if (need_v) {
-      const void* vsrc = vreal ? (const void*)(reinterpret_cast<const float*>(a.V) + rows0)
-                               : (const void*)(reinterpret_cast<const float2*>(a.V) + rows0);
-      bulk_load(SV, vsrc, vbytes, &bars[1]);
-    }
-    if (need_y) bulk_load(SY, a.y + rows0, CHUNK_BYTES, &bars[1]);
-  }
-  auto wait_bar = [&](int i) {   // uniform outcome for the whole CTA
-    if (tid == 0) ok_flag = mbar_wait(&bars[i], 0) ? 1 : 0;
+  };
+  auto wait_bar = [&](int i, uint32_t parity) {   // one outcome for the whole CTA
+    if (tid == 0) ok_flag = mbar_wait(&bars[i], parity) ? 1 : 0;
     __syncthreads();
     ok = ok && ok_flag;
   };
-  // V, y of this thread's point x (row layout)
-  auto vval = [&](int x) -> float2 {
-    if (STAGED) return vreal ? make_float2(reinterpret_cast<const float*>(SV)[rho * PN + x], 0.f)
-                             : SV[rho * PN + x];
-    return ld_v(a.V, row0 + x, vreal);
+  auto refill = [&](int which, int64_t zz) {   // slot free (all threads) -> next plane
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && zz < a.nz) issue(which, zz);
   };
-  auto yval = [&](int x) -> float2 { return STAGED ? SY[rho * PN + x] : a.y[row0 + x]; };
 
-  float2* exr = B + rho * PN;
-  float2 v[16];
-  float acc = 0.f;
-
-  if (do_post) {
-    float2 xr[16];
-    if (STAGED) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        xr[q] = xzero ? make_float2(0.f, 0.f) : a.x_in[row0 + g + 16 * q];
-      wait_bar(0);
-    }
-    // ---- inverse FFT along y on this CTA's 32 columns
+  float2 xr[16];
+  auto prefetch_x = [&](int64_t zz) {    // row layout: x = g + 16 q of row 32 r + rho
+    const int64_t row0 = zz * (int64_t)(PN * PN) + (int64_t)(PR * r + rho) * PN;
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      v[q] = STAGED ? B[(16 * q + w) * PR + l] : a.buf[cblk + (16 * q + w) * PR + l];
-    if (STAGED) __syncthreads();    // B becomes the exchange buffer
-    fft_cols_x<PN, true>(v, B, tw, w, l);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) B[(w + 16 * q) * PR + l] = v[q];   // B[y][xl]
-    cluster.sync();
-    // ---- transpose: this CTA's 32 rows, gathered from all column blocks
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const float2* src = cluster.map_shared_rank(B, q >> 1);
-      v[q] = src[(PR * r + rho) * PR + 16 * (q & 1) + g];       // x = 16 q + g
+      xr[q] = xzero ? make_float2(0.f, 0.f) : a.x_in[row0 + g + 16 * q];
+  };
+
+  if (cid < a.nz) {
+    if (tid == 0) {
+      if (do_post) issue(0, cid);
+      if (need_v) issue(1, cid);
+      if (do_pre) issue(2, cid);
     }
-    cluster.sync();
-    // ---- inverse FFT along x; Delta, update, next B x + y
-    fft_rows_x<PN, true>(v, exr, tw, g);
-    if (STAGED) wait_bar(1);
+    prefetch_x(cid);
+  }
+
+  float acc = 0.f;
+  int it = 0;
+  for (int64_t z = cid; z < a.nz; z += ncl, ++it) {
+    const uint32_t par = uint32_t(it & 1);
+    const int64_t znext = z + ncl;
+    const int64_t row0 = z * (int64_t)(PN * PN) + (int64_t)(PR * r + rho) * PN;
+    float2 v[16];
+    if (do_post) {
+      // ---- inverse FFT y on this CTA's column block (exchange in C)
+      wait_bar(0, par);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = C[(16 * q + w) * PR + l];
+      __syncthreads();
+      fft_cols_x<PN, true>(v, C, tw, w, l);                    // v[q]: y = w + 16 q
+#pragma unroll
+      for (int q = 0; q < 16; ++q) C[(w + 16 * q) * PR + l] = v[q];   // C[y][xl]
+      cluster.sync();
+      // ---- transpose: this CTA's rows from every column block
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float2* src = cluster.map_shared_rank(C, q >> 1);
+        v[q] = src[(PR * r + rho) * PR + 16 * (q & 1) + g];     // x = 16 q + g
+      }
+      cluster.sync();
+      // ---- inverse FFT x (exchange in C), then C takes the next block
+      fft_rows_x<PN, true>(v, C + rho * PN, tw, g);             // v[q]: x = g + 16 q
+      refill(0, znext);
+    }
+    if (need_v) wait_bar(1, par);
+    if (do_pre) wait_bar(2, par);
+    // ---- pointwise: Delta, update, norm, next B x + y (row layout)
     const float al = a.alpha;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int x = g + 16 * q;
-      const int64_t i = row0 + x;
-      const float2 vv = vval(x);
-      const float2 xv = STAGED ? xr[q] : (xzero ? make_float2(0.f, 0.f) : a.x_in[i]);
-      const float ur = v[q].x - xv.x, ui = v[q].y - xv.y;
+      const int x = do_post ? g + 16 * q : 16 * q + g;
+      const int c = rho * PN + x;
+      float2 vv = make_float2(0.f, 0.f);
+      if (need_v)
+        vv = vreal ? make_float2(reinterpret_cast<const float*>(SV)[c], 0.f) : SV[c];
       const float br = 1.f - vv.x, bi = -vv.y;
-      const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
-      acc += dr * dr + di * di;
-      const float2 xn = make_float2(xv.x + al * dr, xv.y + al * di);
-      if (!(a.flags & F_REF)) a.x_out[i] = xn;
+      float2 xn = xr[q];
+      if (do_post) {
+        const float ur = v[q].x - xr[q].x, ui = v[q].y - xr[q].y;
+        const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
+        acc += dr * dr + di * di;
+        xn = make_float2(xr[q].x + al * dr, xr[q].y + al * di);
+        if (!(a.flags & F_REF)) a.x_out[row0 + x] = xn;
+      }
       if (do_pre) {
-        const float2 yv = yval(x);
+        const float2 yv = SY[c];
         v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
       }
     }
-  } else {
-    // prologue: t = (1-V) x + y at x = 16 q + g
-    float2 xr[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      xr[q] = xzero ? make_float2(0.f, 0.f) : a.x_in[row0 + 16 * q + g];
-    if (STAGED) wait_bar(1);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int x = 16 * q + g;
-      float2 t = yval(x);
-      if (!xzero) {
-        const float2 vv = vval(x);
-        const float br = 1.f - vv.x, bi = -vv.y;
-        t.x += br * xr[q].x - bi * xr[q].y;
-        t.y += br * xr[q].y + bi * xr[q].x;
-      }
-      v[q] = t;
+    if (znext < a.nz) prefetch_x(znext);
+    if (!do_pre) {
+      refill(1, need_v ? znext : a.nz);   // V slot free
+      cluster.sync();                     // peers are done with C before it is rewritten
+      continue;
     }
-  }
-
-  if (do_pre) {
-    // ---- forward FFT along x (register order is the stage-1 order for 256)
-    fft_rows_x<PN, false>(v, exr, tw, g);
+    // ---- forward FFT x (exchange in SY, consumed); row results stay in SY
+    __syncthreads();
+    fft_rows_x<PN, false>(v, SY + rho * PN, tw, g);             // v[q]: kx = g + 16 q
 #pragma unroll
-    for (int q = 0; q < 16; ++q) exr[g + 16 * q] = v[q];     // B[row][kx]
+    for (int q = 0; q < 16; ++q) SY[rho * PN + g + 16 * q] = v[q];
     cluster.sync();
-    // ---- transpose: this CTA's 32 columns (kx), gathered from all row blocks
+    // ---- transpose: this CTA's column block from every row block
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const float2* src = cluster.map_shared_rank(B, q >> 1);
+      const float2* src = cluster.map_shared_rank(SY, q >> 1);
       v[q] = src[(16 * (q & 1) + w) * PN + PR * r + l];         // y = 16 q + w
     }
     cluster.sync();
-    // ---- forward FFT along y, store the column block
-    fft_cols_x<PN, false>(v, B, tw, w, l);
+    refill(2, znext);                                            // peers have read SY
+    // ---- forward FFT y (exchange in SV, consumed), store the column block
+    fft_cols_x<PN, false>(v, SV, tw, w, l);                      // v[q]: ky = w + 16 q
+    const int64_t cblk = (z * PC + r) * (int64_t)CHUNK;
 #pragma unroll
     for (int q = 0; q < 16; ++q) a.buf[cblk + (w + 16 * q) * PR + l] = v[q];
+    refill(1, need_v ? znext : a.nz);
   }
 
-  if (STAGED && !ok && tid == 0) {
-    // let late copies land before this CTA's shared memory is released
-    if (do_post) mbar_wait(&bars[0], 0);
-    mbar_wait(&bars[1], 0);
+  if (!ok && tid == 0) {
     a.st->status = ST_TIMEOUT;
     a.st->done = 1;
   }
@@ -280,9 +289,9 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, STAGED ? 
     __syncthreads();
     if (is_last) {
       __threadfence();
-      double s = 0.0;
-      for (unsigned i = threadIdx.x; i < gridDim.x; i += PTHREADS) s += __ldcg(a.partials + i);
-      const double tot = block_sum512(s, red);
+      double sm = 0.0;
+      for (unsigned i = threadIdx.x; i < gridDim.x; i += PTHREADS) sm += __ldcg(a.partials + i);
+      const double tot = block_sum512(sm, red);
       if (threadIdx.x == 0) {
         if (a.st->status != ST_TIMEOUT) finalize_iteration(a.st, a.hist, tot, a.flags);
         a.st->ticket = 0u;
@@ -292,18 +301,11 @@ __global__ void __cluster_dims__(PC, 1, 1) __launch_bounds__(PTHREADS, STAGED ? 
 }
 
 cudaError_t plane_kernel_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PSMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)PSMEM_TMA);
+  return cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSMEM);
 }
 
-cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
-  if (a.staged)
-    k_plane<true><<<(unsigned)(a.nz * PC), PTHREADS, PSMEM_TMA, s>>>(a);
-  else
-    k_plane<false><<<(unsigned)(a.nz * PC), PTHREADS, PSMEM, s>>>(a);
+cudaError_t launch_plane(const PlaneArgs& a, int clusters, cudaStream_t s) {
+  k_plane<<<(unsigned)(clusters * PC), PTHREADS, PSMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -311,7 +313,7 @@ int plane_max_active_clusters() {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(PC * 256, 1, 1);
   cfg.blockDim = dim3(PTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = PSMEM_TMA;
+  cfg.dynamicSmemBytes = PSMEM;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
   attr.val.clusterDim.x = PC;
@@ -320,7 +322,7 @@ int plane_max_active_clusters() {
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_plane<true>, &cfg) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveClusters(&n, k_plane, &cfg) != cudaSuccess) return -1;
   return n;
 }
 

@@ -132,7 +132,7 @@ struct PlaneArgs {
   int nz;
   const float2* x_in;
   float2* x_out;
-  const float2* y;
+  const float2* y;      // bulk-copied: 16-byte aligned
   const void* V;
   float2* buf;          // column-block layout T[z][cb][y][xl]
   const float2* tw;     // W_256^m table (device)
@@ -140,11 +140,10 @@ struct PlaneArgs {
   DevState* st;
   double* hist;
   float alpha;
-  int staged;           // inputs by bulk copy (all pointers 16-byte aligned)
 };
 
 cudaError_t plane_kernel_init();
-cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s);
+cudaError_t launch_plane(const PlaneArgs& a, int clusters, cudaStream_t s);
 int plane_max_active_clusters();
 const float2* twiddle_table_f32();
 

@@ -87,6 +87,14 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
   }
   __syncthreads();
 
+  // the multiply of the outermost axis: this thread's axis frequencies are
+  // the same in every tile, so |p_axis|^2 is evaluated once
+  const bool mul = a.mode == COL_FWD_MUL_INV;
+  float pz2[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) pz2[q] = mul ? axis_p2_f(a.sym, 0, out_index<N>(g, q)) : 0.f;
+  const float b1 = a.sym.b_re + 1.f;
+
   int64_t issued = 0;  // tiles whose loads were issued (thread 0 only)
   if (threadIdx.x == 0) {
     for (; issued < 2 && issued < my; ++issued) {
@@ -131,10 +139,20 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
           p2in = axis_p2_f(a.sym, 1, int(col));
         }
         float2 tmp[N1];
+        if (a.mul == MUL_LINV) {
+          // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
 #pragma unroll
-        for (int q = 0; q < N1; ++q) {
-          const int kk = out_index<N>(g, q);
-          v[q] = cmul(v[q], spectral_factor_f(p2in + axis_p2_f(a.sym, 0, kk), a.sym, a.mul));
+          for (int q = 0; q < N1; ++q) {
+            const float p2 = p2in + pz2[q];
+            const float dr = fmaf(a.sym.a_re, p2, b1);
+            const float di = fmaf(a.sym.a_im, p2, a.sym.b_im);
+            const float sc = __fdividef(a.sym.inv_n, fmaf(dr, dr, di * di));
+            v[q] = cmul(v[q], make_float2(dr * sc, -di * sc));
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < N1; ++q)
+            v[q] = cmul(v[q], spectral_factor_f(p2in + pz2[q], a.sym, a.mul));
         }
         out_to_in<N>(v, tmp);
 #pragma unroll

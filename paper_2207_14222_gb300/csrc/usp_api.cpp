@@ -120,6 +120,7 @@ struct usp_solver {
   Sym<float> symf{};
   Sym<double> symd{};
   const float2* tw32 = nullptr;    // device twiddle table (fused plane pass)
+  int plane_clusters = 0;          // persistent clusters of the fused plane pass
   int num_sms = 0;
   bool maps_ok = false;            // TMA tensor maps of the scratch field
   CUtensorMap map_ax[2];           // [axis]: strided-axis views of s->buf (axis 0, axis 1)
@@ -344,12 +345,13 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
 // ---- fused two-pass schedule (grids nz x 256 x 256, fused3d_kernels.cu)
 
 static bool fused_supported(const usp_solver* s) {
-  return s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256;
+  return s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256 && s->plane_clusters > 0 &&
+         s->maps_ok;
 }
-// Automatic choice: the pencil schedule (measured faster on 256^3 than the
-// current plane-cluster kernel); schedule 2 selects the fused one.
-static bool use_fused(const usp_solver* s) {
-  return s->opt.schedule == 2 && fused_supported(s);
+// Automatic choice: the pencil schedule; schedule 2 selects the fused one
+// (it bulk-copies y, so y must be 16-byte aligned; otherwise pencil).
+static bool use_fused(const usp_solver* s, const float2* y) {
+  return s->opt.schedule == 2 && fused_supported(s) && (((uintptr_t)y & 15u) == 0);
 }
 
 static PlaneArgs plane_args(usp_solver* s, const float2* y, const float2* xin, float2* xout,
@@ -368,10 +370,12 @@ static PlaneArgs plane_args(usp_solver* s, const float2* y, const float2* xin, f
   p.st = s->st;
   p.hist = s->hist;
   p.alpha = (float)s->alpha;
-  // bulk copies need 16-byte aligned sources
-  const uintptr_t al = (uintptr_t)y | (uintptr_t)xin | (uintptr_t)s->V | (uintptr_t)s->buf;
-  p.staged = (!s->opt.no_tma && (al & 15u) == 0) ? 1 : 0;
   return p;
+}
+
+static std::function<cudaError_t(cudaStream_t)> plane_pass(usp_solver* s, const PlaneArgs& p) {
+  const int clusters = std::max(1, std::min(s->plane_clusters, s->n[0]));
+  return [=](cudaStream_t t) { return launch_plane(p, clusters, t); };
 }
 
 static std::vector<PassLaunch> fused_prologue(usp_solver* s, const float2* y, const float2* xin,
@@ -379,8 +383,7 @@ static std::vector<PassLaunch> fused_prologue(usp_solver* s, const float2* y, co
   const double vb = s->vreal ? 4.0 : 8.0;
   const bool xz = (flags & F_XZERO) != 0;
   PlaneArgs p = plane_args(s, y, xin, nullptr, flags & ~F_REF, PL_PRE);
-  return {{"plane_pre", 16.0 + (xz ? 0.0 : 8.0 + vb),
-           [=](cudaStream_t t) { return launch_plane(p, t); }}};
+  return {{"plane_pre", 16.0 + (xz ? 0.0 : 8.0 + vb), plane_pass(s, p)}};
 }
 
 static std::vector<PassLaunch> fused_passes(usp_solver* s, const float2* y, const float2* xin,
@@ -392,24 +395,23 @@ static std::vector<PassLaunch> fused_passes(usp_solver* s, const float2* y, cons
   P.push_back({"z_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
   if (ref) {
     PlaneArgs p = plane_args(s, y, xin, xout, flags, PL_POST);
-    P.push_back({"plane_post", 8.0 + vb, [=](cudaStream_t t) { return launch_plane(p, t); }});
+    P.push_back({"plane_post", 8.0 + vb, plane_pass(s, p)});
   } else {
     PlaneArgs p = plane_args(s, y, xin, xout, flags, PL_FULL);
-    P.push_back({"plane_full", 32.0 + vb + (xz ? 0.0 : 8.0),
-                 [=](cudaStream_t t) { return launch_plane(p, t); }});
+    P.push_back({"plane_full", 32.0 + vb + (xz ? 0.0 : 8.0), plane_pass(s, p)});
   }
   return P;
 }
 
 static std::vector<PassLaunch> iteration_passes(usp_solver* s, const float2* y, const float2* xin,
                                                 float2* xout, int flags) {
-  if (use_fused(s)) return fused_passes(s, y, xin, xout, flags);
+  if (use_fused(s, y)) return fused_passes(s, y, xin, xout, flags);
   return pencil_passes(s, y, xin, xout, flags);
 }
 
 static std::vector<PassLaunch> prologue_passes(usp_solver* s, const float2* y, const float2* xin,
                                                int flags) {
-  if (use_fused(s)) return fused_prologue(s, y, xin, flags);
+  if (use_fused(s, y)) return fused_prologue(s, y, xin, flags);
   return pencil_prologue(s, y, xin, flags);
 }
 
@@ -611,6 +613,7 @@ extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol*
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   if (s->num_sms < 1) s->num_sms = 1;
   build_maps(s);
+  if (s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256) s->plane_clusters = plane_max_active_clusters();
   *out = s;
   return USP_OK;
 #undef CREATE_TRY
