@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--cpu-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, plain and roofline legs")
+    p.add_argument("--batch", type=int, default=64,
+                   help="problems of the batched leg (2-D 128x128 media; 0 skips it)")
+    p.add_argument("--batch-n", type=int, default=128)
     return p.parse_args()
 
 
@@ -347,6 +350,52 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
                         "min_rel_residual": float(h.min()), "argmin": int(h.argmin()) + 1,
                         "iter_per_s": r["iterations"] / dt,
                         "s_to_min_residual": dt * (int(h.argmin()) + 1) / r["iterations"]}
+    if args.batch > 0:
+        out["batched"] = batched_leg(args, torch, dev)
+    return out
+
+
+def batched_leg(args, torch, dev):
+    """Many small 2-D problems (the 128x128 medium distribution, one seed
+    each): solved together by one batch solver vs one solver per problem,
+    both to the same tolerance with refinement."""
+    from paper_2207_14222_gb300 import canon, inputs
+    from paper_2207_14222_gb300.solver import BatchSolver, Solver
+    n, B = args.batch_n, args.batch
+    cfs = [canon.canonical(inputs.helmholtz_2d(n, seed=1000 + j, abl_width=max(4, n // 8)))
+           for j in range(B)]
+    V = torch.from_numpy(np.stack([cf["V"] for cf in cfs])).to(dev)
+    y = torch.from_numpy(np.stack([cf["y"] for cf in cfs])).to(dev)
+    a = [cf["a"] for cf in cfs]
+    b = [cf["b"] for cf in cfs]
+
+    def batched():
+        with BatchSolver((n, n), a, b, V) as s:
+            _, res = s.solve(y, tol=args.tol, maxit=args.maxit)
+        return res
+
+    def one_by_one():
+        res = []
+        for j in range(B):
+            with Solver((n, n), a[j], b[j], V[j]) as s:
+                _, r = s.solve(y[j], tol=args.tol, maxit=args.maxit)
+            res.append(r)
+        return res
+
+    out = {"problems": B, "grid": [n, n], "tol": args.tol,
+           "step": "create + solve every problem to tol + destroy"}
+    for name, fn in (("batched", batched), ("one_by_one", one_by_one)):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        its = [r["iterations"] for r in res]
+        out[name] = {"s": dt, "problem_iter_per_s": sum(its) / dt,
+                     "converged": sum(int(r["converged"]) for r in res),
+                     "iterations_min_max": [min(its), max(its)]}
+    out["speedup"] = out["one_by_one"]["s"] / out["batched"]["s"]
     return out
 
 

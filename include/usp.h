@@ -128,6 +128,48 @@ usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol* lsym,
                              const void* V, int32_t V_is_real, double alpha,
                              void* cuda_stream, usp_solver** out);
 
+/* ---- batches of problems on one grid --------------------------------------
+ *
+ * `count` independent problems A_j = L_j + V_j on the same grid, solved
+ * together: every pass of Algorithm 1 (Sec. 2.1) runs once over all problems,
+ * each with its own symbol, step, convergence test, residual history and FP64
+ * refinement.  The paper solves one problem at a time; the batch is this
+ * library's throughput form of the same iteration, and each problem follows
+ * exactly the path it would take alone.
+ *   lsyms, alphas: host arrays of `count` (alphas[j] <= 0: automatic).
+ *   V: device pointer, count * N values (problem j at offset j * N), complex64
+ *      or float32 (V_is_real, one setting for the whole batch).
+ * count >= 1; count > 1 needs a 2-D or 3-D grid whose number of lines along
+ * the last axis per problem, N / n_last, is a multiple of 256 * m / n_last
+ * with m = 2^ceil(log2(n_last) / 2) (16 lines for n_last = 256, 32 for 64
+ * and 128), so that no block of the line passes straddles two problems
+ * (USP_ERR_UNSUPPORTED_SIZE otherwise).  Validation as usp_solver_create, for every problem.  A batch
+ * solver is solved with usp_batch_solve (usp_solve and usp_solve_host
+ * return USP_ERR_INVALID_ARG); usp_apply_A, usp_residual and usp_time_passes
+ * act on the whole batch (usp_residual's rel_out is over all problems). */
+usp_status usp_batch_create(const usp_grid* grid, int32_t count,
+                            const usp_lsymbol* lsyms, const void* V,
+                            int32_t V_is_real, const double* alphas,
+                            void* cuda_stream, usp_solver** out);
+
+/* Algorithm 1 for every problem of a batch solver.  y, x: device pointers,
+ * count * N complex64 (layout as V).  ref_norms: host array of count (<= 0:
+ * automatic) or NULL (all automatic).  results, statuses: host arrays of
+ * count, or NULL; statuses[j] is what usp_solve would return for problem j
+ * alone.  Returns USP_OK when every problem converged, else the status of
+ * the lowest-numbered problem that did not (its message in usp_last_error).
+ * Synchronous. */
+usp_status usp_batch_solve(usp_solver* s, const void* y, void* x,
+                           int32_t use_x0, double tol, int32_t maxit,
+                           const double* ref_norms, usp_result* results,
+                           usp_status* statuses);
+
+/* Residual history of problem `problem` of the last solve (as
+ * usp_residual_history, which reports problem 0). */
+usp_status usp_batch_history(const usp_solver* s, int32_t problem,
+                             double* host_out, int32_t capacity,
+                             int32_t* n_out);
+
 /* Replace the options of a solver (host pointer, copied). */
 usp_status usp_solver_set_options(usp_solver* s, const usp_options* opt);
 

@@ -63,6 +63,11 @@ _P = ctypes.POINTER
 _SIGNATURES = {
     "usp_solver_create": (c_int32, [_P(Grid), _P(LSymbol), c_void_p, c_int32, c_double,
                                     c_void_p, _P(c_void_p)]),
+    "usp_batch_create": (c_int32, [_P(Grid), c_int32, _P(LSymbol), c_void_p, c_int32,
+                                   _P(c_double), c_void_p, _P(c_void_p)]),
+    "usp_batch_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
+                                  _P(c_double), _P(Result), _P(c_int32)]),
+    "usp_batch_history": (c_int32, [c_void_p, c_int32, _P(c_double), c_int32, _P(c_int32)]),
     "usp_solver_set_options": (c_int32, [c_void_p, _P(Options)]),
     "usp_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
                             c_double, _P(Result)]),

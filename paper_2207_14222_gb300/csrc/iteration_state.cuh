@@ -70,4 +70,27 @@ __device__ __forceinline__ void finalize_iteration(DevState* st, double* hist, d
   }
 }
 
+// The symbol of problem p (batch) or the scalar one.
+__device__ __forceinline__ Sym<float> problem_sym(const Sym<float>& s, const Batch& b, int p) {
+  Sym<float> r = s;
+  if (b.sym32) {
+    const float4 c = b.sym32[p];
+    r.a_re = c.x;
+    r.a_im = c.y;
+    r.b_re = c.z;
+    r.b_im = c.w;
+  }
+  return r;
+}
+__device__ __forceinline__ Sym<double> problem_sym(const Sym<double>& s, const Batch& b, int p) {
+  Sym<double> r = s;
+  if (b.sym64) {
+    r.a_re = b.sym64[4 * p];
+    r.a_im = b.sym64[4 * p + 1];
+    r.b_re = b.sym64[4 * p + 2];
+    r.b_im = b.sym64[4 * p + 3];
+  }
+  return r;
+}
+
 }  // namespace usp

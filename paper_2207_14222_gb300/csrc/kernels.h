@@ -87,6 +87,20 @@ struct Sym {
   int ndim;
 };
 
+// Independent problems on the same grid, stacked along a new slowest axis.
+// count == 1 is the single-problem solver (the kernels then use the scalar
+// symbol and step of their arguments).  Every block or tile belongs to one
+// problem: rows_per and outer_per are multiples of the kernels' tile sizes.
+struct Batch {
+  int count;              // problems
+  int64_t rows_per;       // last-axis lines per problem (rows kernels)
+  int64_t outer_per;      // outer slabs per problem (strided-axis kernels)
+  const float4* sym32;    // per problem (a_re, a_im, b_re, b_im), or nullptr
+  const double* sym64;    // per problem 4 doubles, or nullptr
+  const float* alpha;     // per problem step, or nullptr
+  int hist_stride;        // history entries per problem
+};
+
 template <typename T>
 struct RowsArgs {
   int mode;             // RowMode bit set
@@ -104,6 +118,7 @@ struct RowsArgs {
   double* hist;
   T alpha;
   Sym<T> sym;
+  Batch bt;
 };
 
 template <typename T>
@@ -117,6 +132,7 @@ struct ColsArgs {
   void* buf;            // complex scratch of type cplx_of<T>, in place
   DevState* st;
   Sym<T> sym;
+  Batch bt;
 };
 
 // Plane pass of the fused schedule (fused3d_kernels.cu), grids nz x 256 x 256.
@@ -158,6 +174,7 @@ struct ColsTmaArgs {
   DevState* st;
   const float2* tw;     // W_256^m table (device)
   Sym<float> sym;
+  Batch bt;
 };
 cudaError_t cols_tma_init();
 cudaError_t launch_cols_tma(int n, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
@@ -174,10 +191,11 @@ struct RowsTmaArgs {
   const void* V;
   float2* buf;
   const float2* tw;     // W_256^m table (device)
-  double* partials;     // one double per CTA
+  double* partials;     // one double per CTA (single problem) or per tile (batch)
   DevState* st;
   double* hist;
   float alpha;
+  Batch bt;
 };
 cudaError_t rows_tma_init();
 cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s);
@@ -196,10 +214,14 @@ cudaError_t init_twiddles();
 // their reduction into out[3] (device).
 cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials,
                            int nblocks, double* out, cudaStream_t s);
-// x += z (complex64).
-cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s);
-// Sum `count` partial pairs (2 doubles per block) into out[2].
-cudaError_t launch_sum_pairs(const double* partials, int count, double* out, cudaStream_t s);
+// x += z (complex64); with `mask` (per problem, n_per points each) only where
+// mask[problem] != 0.
+cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s,
+                         const int* mask = nullptr, int64_t n_per = 0);
+// Sum `groups` consecutive runs of `count` partial pairs (2 doubles per
+// block) into out[2 * group], out[2 * group + 1].
+cudaError_t launch_sum_pairs(const double* partials, int count, int groups, double* out,
+                             cudaStream_t s);
 // Record the message usp_last_error() returns on this thread (usp_api.cpp).
 void set_last_error(const char* fmt, ...);
 // Copy a real float32 or complex64 potential into solver storage.

@@ -69,25 +69,28 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-// Block partial of ||Delta||^2, then the last block to finish sums all
-// partials in a fixed order (deterministic) and updates the state.
+// Block partial of ||Delta||^2 into partials[part_index]; the last of the
+// problem's part_count blocks to finish sums the problem's partials
+// [part_first, part_first + part_count) in a fixed order (deterministic) and
+// updates its state.
 template <int THREADS>
-__device__ void reduce_and_finalize(double acc, double* partials, DevState* st, double* hist,
-                                    int flags) {
+__device__ void reduce_and_finalize(double acc, double* partials, int64_t part_index,
+                                    int64_t part_first, int64_t part_count, DevState* st,
+                                    double* hist, int flags) {
   __shared__ double red[THREADS / 32];
   __shared__ int is_last;
   const double bs = block_sum<THREADS>(acc, red);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bs;
+    partials[part_index] = bs;
     __threadfence();
     const unsigned t = atomicAdd(&st->ticket, 1u);
-    is_last = (t == gridDim.x - 1);
+    is_last = (t == (unsigned)(part_count - 1));
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
   double s = 0.0;
-  for (unsigned i = threadIdx.x; i < gridDim.x; i += THREADS) s += __ldcg(partials + i);
+  for (int64_t i = threadIdx.x; i < part_count; i += THREADS) s += __ldcg(partials + part_first + i);
   const double tot = block_sum<THREADS>(s, red);
   if (threadIdx.x == 0) {
     finalize_iteration(st, hist, tot, flags);
@@ -157,7 +160,10 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* ex = tw + N;
 
-  if (!(a.flags & F_NOSTATE) && a.st->done) return;
+  // the problem of this block (blocks never straddle problems)
+  const int p = a.bt.count > 1 ? int((int64_t)blockIdx.x * F / a.bt.rows_per) : 0;
+  DevState* st = a.st + p;
+  if (!(a.flags & F_NOSTATE) && st->done) return;
 
   const int tid = threadIdx.x, f = tid / G, g = tid % G;
   const int64_t row = (int64_t)blockIdx.x * F + f;
@@ -199,10 +205,11 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
   // ---- transforms
   if (a.mode & R_FWD) fft_rows<N, false>(v, exr, tw, g);
   if (a.mode & R_MUL) {
+    const Sym<T> sy = problem_sym(a.sym, a.bt, p);
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       const int k = out_index<N>(g, q);
-      v[q] = cmul(v[q], spectral_factor<T, V>(axis_p2(a.sym, 0, k), a.sym, a.mul));
+      v[q] = cmul(v[q], spectral_factor<T, V>(axis_p2(sy, 0, k), sy, a.mul));
     }
   }
   if (a.mode & R_INV) {
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
     float acc = 0.f;
     const bool then_pre = (a.mode & R_THEN_PRE_FWD) != 0;
     if (active) {
-      const float al = float(a.alpha);
+      const float al = a.bt.alpha ? a.bt.alpha[p] : float(a.alpha);
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
         const int64_t i = base + out_index<N>(g, q);
@@ -259,7 +266,9 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
           reinterpret_cast<V*>(a.buf)[base + out_index<N>(g, q)] = v[q];
       }
     }
-    reduce_and_finalize<THREADS>((double)acc, a.partials, a.st, a.hist, a.flags);
+    const int64_t bpp = a.bt.count > 1 ? a.bt.rows_per / F : (int64_t)gridDim.x;
+    reduce_and_finalize<THREADS>((double)acc, a.partials, blockIdx.x, p * bpp, bpp, st,
+                                 a.hist + (int64_t)p * a.bt.hist_stride, a.flags);
     return;
   }
   if (a.mode & R_OUT_RESID) {
@@ -324,10 +333,11 @@ __global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) 
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* ex = tw + N;
 
-  if (!(a.flags & F_NOSTATE) && a.st->done) return;
+  const int64_t ib = blockIdx.x % a.inner_blocks, o = blockIdx.x / a.inner_blocks;
+  const int p = a.bt.count > 1 ? int(o / a.bt.outer_per) : 0;
+  if (!(a.flags & F_NOSTATE) && a.st[p].done) return;
 
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int64_t ib = blockIdx.x % a.inner_blocks, o = blockIdx.x / a.inner_blocks;
   const int64_t col = ib * 32 + lane;
   const bool active = col < a.inner;
   const int64_t base = o * (int64_t)N * a.inner + col;
@@ -347,21 +357,22 @@ __global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) 
     if (a.mode == COL_FWD_MUL_INV) {
       // This pass runs on axis 0 after all faster axes were transformed, so
       // the column index decomposes into their frequency indices.
+      const Sym<T> sy = problem_sym(a.sym, a.bt, p);
       T p2in = T(0);
       if (a.flags & F_CBLOCK) {
         // column-block layout of the fused schedule: col = (cb * 256 + ky) * 32 + xl
-        p2in = axis_p2(a.sym, 2, int((col >> 13) * 32 + (col & 31))) +
-               axis_p2(a.sym, 1, int((col >> 5) & 255));
-      } else if (a.sym.ndim == 3) {
-        p2in = axis_p2(a.sym, 2, int(col % a.sym.n[2])) + axis_p2(a.sym, 1, int(col / a.sym.n[2]));
-      } else if (a.sym.ndim == 2) {
-        p2in = axis_p2(a.sym, 1, int(col));
+        p2in = axis_p2(sy, 2, int((col >> 13) * 32 + (col & 31))) +
+               axis_p2(sy, 1, int((col >> 5) & 255));
+      } else if (sy.ndim == 3) {
+        p2in = axis_p2(sy, 2, int(col % sy.n[2])) + axis_p2(sy, 1, int(col / sy.n[2]));
+      } else if (sy.ndim == 2) {
+        p2in = axis_p2(sy, 1, int(col));
       }
       V t[N1];
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
         const int k = out_index<N>(g, q);
-        v[q] = cmul(v[q], spectral_factor<T, V>(p2in + axis_p2(a.sym, 0, k), a.sym, a.mul));
+        v[q] = cmul(v[q], spectral_factor<T, V>(p2in + axis_p2(sy, 0, k), sy, a.mul));
       }
       out_to_in<N>(v, t);
 #pragma unroll
@@ -509,26 +520,30 @@ cudaError_t init_twiddles() {
 
 // -------------------------------------------------------- auxiliaries ---
 
+// Statistics of V for validation and alpha = Re[B^-1] = min_r Re 1/(1 - V):
+// per-thread FP32 (V is FP32 data; Re 1/(1-V) = (1-Re V)/|1-V|^2 needs no
+// more), block and grid reductions in FP64.
 __global__ void k_v_stats(const void* V, int vreal, int64_t n, double* partials) {
-  double vmax = 0.0, amin = 1e300, bad = 0.0;
+  float vmax = 0.f, amin = 3.0e38f;
+  int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float2 v = vreal ? make_float2(reinterpret_cast<const float*>(V)[i], 0.f)
-                     : reinterpret_cast<const float2*>(V)[i];
+    const float2 v = vreal ? make_float2(reinterpret_cast<const float*>(V)[i], 0.f)
+                           : reinterpret_cast<const float2*>(V)[i];
     if (!isfinite(v.x) || !isfinite(v.y)) {
-      bad += 1.0;
+      ++bad;
       continue;
     }
-    const double vr = v.x, vi = v.y;
-    vmax = fmax(vmax, sqrt(vr * vr + vi * vi));
-    const double br = 1.0 - vr;                      // B = 1 - V
-    amin = fmin(amin, br / (br * br + vi * vi));     // Re 1/B
+    vmax = fmaxf(vmax, sqrtf(v.x * v.x + v.y * v.y));
+    const float br = 1.f - v.x;                       // B = 1 - V
+    amin = fminf(amin, br / (br * br + v.y * v.y));   // Re 1/B
   }
-  __shared__ double r0[8], r1[8], r2[8];
+  __shared__ float r0[8], r1[8];
+  __shared__ int r2[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
-    amin = fmin(amin, __shfl_down_sync(0xffffffffu, amin, o));
+    vmax = fmaxf(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    amin = fminf(amin, __shfl_down_sync(0xffffffffu, amin, o));
     bad += __shfl_down_sync(0xffffffffu, bad, o);
   }
   const int w = threadIdx.x >> 5;
@@ -540,8 +555,8 @@ __global__ void k_v_stats(const void* V, int vreal, int64_t n, double* partials)
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-      r0[0] = fmax(r0[0], r0[i]);
-      r1[0] = fmin(r1[0], r1[i]);
+      r0[0] = fmaxf(r0[0], r0[i]);
+      r1[0] = fminf(r1[0], r1[i]);
       r2[0] += r2[i];
     }
     partials[3 * blockIdx.x] = r0[0];
@@ -551,58 +566,77 @@ __global__ void k_v_stats(const void* V, int vreal, int64_t n, double* partials)
 }
 
 __global__ void k_v_stats_final(const double* partials, int nb, double* out) {
-  if (threadIdx.x != 0) return;
   double vmax = 0.0, amin = 1e300, bad = 0.0;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = threadIdx.x; b < nb; b += 256) {
     vmax = fmax(vmax, partials[3 * b]);
     amin = fmin(amin, partials[3 * b + 1]);
     bad += partials[3 * b + 2];
   }
-  out[0] = vmax;
-  out[1] = amin;
-  out[2] = bad;
+  __shared__ double s0[256], s1[256], s2[256];
+  s0[threadIdx.x] = vmax;
+  s1[threadIdx.x] = amin;
+  s2[threadIdx.x] = bad;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      s0[threadIdx.x] = fmax(s0[threadIdx.x], s0[threadIdx.x + h]);
+      s1[threadIdx.x] = fmin(s1[threadIdx.x], s1[threadIdx.x + h]);
+      s2[threadIdx.x] += s2[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s0[0];
+    out[1] = s1[0];
+    out[2] = s2[0];
+  }
 }
 
 cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials, int nblocks,
                            double* out, cudaStream_t s) {
   k_v_stats<<<nblocks, 256, 0, s>>>(V, vreal, n, partials);
-  k_v_stats_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+  k_v_stats_final<<<1, 256, 0, s>>>(partials, nblocks, out);
   return cudaGetLastError();
 }
 
-__global__ void k_axpy1(float2* x, const float2* z, int64_t n) {
+__global__ void k_axpy1(float2* x, const float2* z, int64_t n, const int* mask, int64_t n_per) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (mask && !mask[i / n_per]) continue;
     const float2 a = x[i], b = z[i];
     x[i] = make_float2(a.x + b.x, a.y + b.y);
   }
 }
 
-cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s) {
+cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s, const int* mask,
+                         int64_t n_per) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  k_axpy1<<<(unsigned)blocks, 256, 0, s>>>(x, z, n);
+  k_axpy1<<<(unsigned)blocks, 256, 0, s>>>(x, z, n, mask, n_per > 0 ? n_per : n);
   return cudaGetLastError();
 }
 
+// Block b sums the `count` partial pairs of group b (2 doubles per block).
 __global__ void k_sum_pairs(const double* partials, int count, double* out) {
   __shared__ double red[8];
+  const double* pp = partials + 2 * (int64_t)blockIdx.x * count;
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < count; i += 256) {
-    a += partials[2 * i];
-    b += partials[2 * i + 1];
+    a += pp[2 * i];
+    b += pp[2 * i + 1];
   }
   const double sa = block_sum<256>(a, red);
   const double sb = block_sum<256>(b, red);
   if (threadIdx.x == 0) {
-    out[0] = sa;
-    out[1] = sb;
+    out[2 * blockIdx.x] = sa;
+    out[2 * blockIdx.x + 1] = sb;
   }
 }
 
-cudaError_t launch_sum_pairs(const double* partials, int count, double* out, cudaStream_t s) {
-  k_sum_pairs<<<1, 256, 0, s>>>(partials, count, out);
+cudaError_t launch_sum_pairs(const double* partials, int count, int groups, double* out,
+                             cudaStream_t s) {
+  k_sum_pairs<<<groups, 256, 0, s>>>(partials, count, out);
   return cudaGetLastError();
 }
 

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
   __shared__ __align__(8) uint64_t full[SLOTS];
   __shared__ int ok_flag;
 
-  if (!(a.flags & F_NOSTATE) && a.st->done) return;
+  const bool batched = a.bt.count > 1;
+  if (!batched && !(a.flags & F_NOSTATE) && a.st->done) return;
 
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int64_t t0 = blockIdx.x, stride = gridDim.x;
@@ -93,7 +94,6 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
   float pz2[N1];
 #pragma unroll
   for (int q = 0; q < N1; ++q) pz2[q] = mul ? axis_p2_f(a.sym, 0, out_index<N>(g, q)) : 0.f;
-  const float b1 = a.sym.b_re + 1.f;
 
   int64_t issued = 0;  // tiles whose loads were issued (thread 0 only)
   if (threadIdx.x == 0) {
@@ -118,6 +118,27 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
     float2* slot = slots + s * TILE;
     const int64_t t = t0 + k * stride;
     const int64_t col = (t % a.inner_blocks) * 32 + lane;
+    // batch: the tile's problem; a finished problem's tiles are left as they are
+    const int pb = batched ? int((t / a.inner_blocks) / a.bt.outer_per) : 0;
+    const bool skip = batched && !(a.flags & F_NOSTATE) && a.st[pb].done;
+    if (skip) {
+      __syncthreads();  // every thread has seen the slot state before it is reloaded
+      if (threadIdx.x == 0) {
+        bulk_commit();  // empty group: one group per tile keeps the slot accounting
+        if (issued < my) {
+          bulk_wait_read<1>();
+          const int s2 = int(issued % SLOTS);
+          const int64_t t2 = t0 + issued * stride;
+          mbar_arrive_expect_tx(&full[s2], TILE_BYTES);
+          tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * 32), 0,
+                      int(t2 / a.inner_blocks), &full[s2]);
+          ++issued;
+        }
+      }
+      continue;
+    }
+    const Sym<float> sy = problem_sym(a.sym, a.bt, pb);
+    const float b1 = sy.b_re + 1.f;
     float2 v[N1];
 #pragma unroll
     for (int q = 0; q < N1; ++q) v[q] = slot[in_index<N>(g, q) * 32 + lane];
@@ -130,13 +151,12 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
         // outermost axis: the column index holds the faster axes' frequencies
         float p2in = 0.f;
         if (a.flags & F_CBLOCK) {
-          p2in = axis_p2_f(a.sym, 2, int((col >> 13) * 32 + (col & 31))) +
-                 axis_p2_f(a.sym, 1, int((col >> 5) & 255));
-        } else if (a.sym.ndim == 3) {
-          p2in = axis_p2_f(a.sym, 2, int(col % a.sym.n[2])) +
-                 axis_p2_f(a.sym, 1, int(col / a.sym.n[2]));
-        } else if (a.sym.ndim == 2) {
-          p2in = axis_p2_f(a.sym, 1, int(col));
+          p2in = axis_p2_f(sy, 2, int((col >> 13) * 32 + (col & 31))) +
+                 axis_p2_f(sy, 1, int((col >> 5) & 255));
+        } else if (sy.ndim == 3) {
+          p2in = axis_p2_f(sy, 2, int(col % sy.n[2])) + axis_p2_f(sy, 1, int(col / sy.n[2]));
+        } else if (sy.ndim == 2) {
+          p2in = axis_p2_f(sy, 1, int(col));
         }
         float2 tmp[N1];
         if (a.mul == MUL_LINV) {
@@ -144,15 +164,15 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
 #pragma unroll
           for (int q = 0; q < N1; ++q) {
             const float p2 = p2in + pz2[q];
-            const float dr = fmaf(a.sym.a_re, p2, b1);
-            const float di = fmaf(a.sym.a_im, p2, a.sym.b_im);
-            const float sc = __fdividef(a.sym.inv_n, fmaf(dr, dr, di * di));
+            const float dr = fmaf(sy.a_re, p2, b1);
+            const float di = fmaf(sy.a_im, p2, sy.b_im);
+            const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, di * di));
             v[q] = cmul(v[q], make_float2(dr * sc, -di * sc));
           }
         } else {
 #pragma unroll
           for (int q = 0; q < N1; ++q)
-            v[q] = cmul(v[q], spectral_factor_f(p2in + pz2[q], a.sym, a.mul));
+            v[q] = cmul(v[q], spectral_factor_f(p2in + pz2[q], sy, a.mul));
         }
         out_to_in<N>(v, tmp);
 #pragma unroll
@@ -185,8 +205,10 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
     if (failed) {
       // let the loads still in flight land before the CTA's shared memory goes
       for (int64_t j = k; j < issued; ++j) mbar_wait(&full[j % SLOTS], uint32_t((j / SLOTS) & 1));
-      a.st->status = ST_TIMEOUT;
-      a.st->done = 1;
+      for (int q = 0; q < (batched ? a.bt.count : 1); ++q) {
+        a.st[q].status = ST_TIMEOUT;
+        a.st[q].done = 1;
+      }
     }
   }
 }
@@ -239,7 +261,8 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
   __shared__ double red[16];
   __shared__ int is_last, ok_flag;
 
-  if (a.st->done) return;
+  const bool batched = a.bt.count > 1;
+  if (!batched && a.st->done) return;
 
   const int tid = threadIdx.x, f = tid / G, g = tid % G;
   const bool xzero = (a.flags & F_XZERO) != 0;
@@ -307,7 +330,10 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
   for (int64_t k = 0; k < my; ++k) {
     const uint32_t par = uint32_t(k & 1);
     const int64_t row = first_row(k) + f;
-    const bool act = row < a.nrows;
+    // batch: the tile's problem; a finished problem's tiles change nothing
+    const int pb = batched ? int(first_row(k) / a.bt.rows_per) : 0;
+    const bool pdone = batched && a.st[pb].done;
+    const bool act = row < a.nrows && !pdone;
     wait_bar(0, par);
     float2 v[N1];
 #pragma unroll
@@ -320,7 +346,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
     wait_bar(1, par);
     wait_bar(2, par);
     // Delta = (1-V)(u - x); x += alpha Delta; next t = (1-V) x + y
-    const float al = a.alpha;
+    const float al = batched && a.bt.alpha ? a.bt.alpha[pb] : a.alpha;
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       const int c = f * N + out_index<N>(g, q);
@@ -351,12 +377,41 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
       for (int q = 0; q < N1; ++q) a.buf[row * N + out_index<N>(g, q)] = v[q];
     }
     release_then(2, k + 1);
+    if (batched && !pdone) {
+      // per-tile partial; the last tile of the problem finalises it
+      double dv = (double)acc;
+      acc = 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dv += __shfl_down_sync(0xffffffffu, dv, o);
+      if ((tid & 31) == 0) red[tid >> 5] = dv;
+      __syncthreads();
+      if (tid == 0) {
+        double bs = 0.0;
+        for (int i = 0; i < 16; ++i) bs += red[i];
+        const int64_t tg = t0 + k * stride, tpp = a.bt.rows_per / F;
+        a.partials[tg] = bs;
+        __threadfence();
+        const unsigned tk = atomicAdd(&a.st[pb].ticket, 1u);
+        if (tk == (unsigned)(tpp - 1)) {
+          __threadfence();
+          double tot = 0.0;
+          for (int64_t i = 0; i < tpp; ++i) tot += __ldcg(a.partials + pb * tpp + i);
+          if (a.st[pb].status != ST_TIMEOUT)
+            finalize_iteration(a.st + pb, a.hist + (int64_t)pb * a.bt.hist_stride, tot, a.flags);
+          a.st[pb].ticket = 0u;
+        }
+      }
+      __syncthreads();
+    }
   }
 
   if (!ok && tid == 0) {
-    a.st->status = ST_TIMEOUT;
-    a.st->done = 1;
+    for (int q = 0; q < (batched ? a.bt.count : 1); ++q) {
+      a.st[q].status = ST_TIMEOUT;
+      a.st[q].done = 1;
+    }
   }
+  if (batched) return;
   // ||Delta||^2: block partial, the last block finalises (fixed order)
   double dv = (double)acc;
 #pragma unroll

@@ -121,6 +121,15 @@ struct usp_solver {
   Sym<double> symd{};
   const float2* tw32 = nullptr;    // device twiddle table (fused plane pass)
   int plane_clusters = 0;          // persistent clusters of the fused plane pass
+  int B = 1;                       // independent problems on this grid (batch)
+  int64_t NB = 0;                  // B * N
+  float4* bsym32 = nullptr;        // per-problem symbols (B > 1), device
+  double* bsym64 = nullptr;
+  float* balpha = nullptr;         // per-problem steps (B > 1), device
+  int* bmask = nullptr;            // problems refined in the current phase, device
+  int* bmask_host = nullptr;       // pinned mirror
+  std::vector<double> alphas;      // per problem
+  std::vector<std::vector<double>> histories;   // per problem, last solve
   int num_sms = 0;
   bool maps_ok = false;            // TMA tensor maps of the scratch field
   CUtensorMap map_ax[2];           // [axis]: strided-axis views of s->buf (axis 0, axis 1)
@@ -172,7 +181,7 @@ static void build_maps(usp_solver* s) {
     int64_t inner = 1, outer = 1;
     for (int ax = axis + 1; ax < s->ndim; ++ax) inner *= s->n[ax];
     for (int ax = 0; ax < axis; ++ax) outer *= s->n[ax];
-    ok = ok && encode_cols_map(&s->map_ax[axis], s->buf, inner, s->n[axis], outer);
+    ok = ok && encode_cols_map(&s->map_ax[axis], s->buf, inner, s->n[axis], outer * s->B);
   }
   s->maps_ok = ok;
 }
@@ -181,15 +190,30 @@ static void build_maps(usp_solver* s) {
 
 static int64_t rows_grid_f32(const usp_solver* s) {
   const int nx = s->n[s->ndim - 1];
-  const int64_t nrows = s->N / nx;
+  const int64_t nrows = s->NB / nx;
   const int F = rows_per_block_f32(nx);
   return (nrows + F - 1) / F;
 }
 static int64_t rows_grid_f64(const usp_solver* s) {
   const int nx = s->n[s->ndim - 1];
-  const int64_t nrows = s->N / nx;
+  const int64_t nrows = s->NB / nx;
   const int F = rows_per_block_f64(nx);
   return (nrows + F - 1) / F;
+}
+
+// Batch descriptor for a pass: outer slabs per problem (strided-axis passes).
+static Batch batch_desc(const usp_solver* s, int64_t outer_per) {
+  Batch b{};
+  b.count = s->B;
+  b.rows_per = s->N / s->n[s->ndim - 1];
+  b.outer_per = outer_per;
+  b.hist_stride = s->hist_cap;
+  if (s->B > 1) {
+    b.sym32 = s->bsym32;
+    b.sym64 = s->bsym64;
+    b.alpha = s->balpha;
+  }
+  return b;
 }
 
 template <typename T>
@@ -202,6 +226,8 @@ static ColsArgs<T> cols_args(const usp_solver* s, int axis, int mode, int mul, i
   int64_t inner = 1, outer = 1;
   for (int ax = axis + 1; ax < s->ndim; ++ax) inner *= s->n[ax];
   for (int ax = 0; ax < axis; ++ax) outer *= s->n[ax];
+  c.bt = batch_desc(s, outer);
+  outer *= s->B;  // problems are stacked along a new slowest axis
   c.inner = inner;
   c.outer = outer;
   c.inner_blocks = (inner + 31) / 32;
@@ -226,6 +252,7 @@ static std::function<cudaError_t(cudaStream_t)> cols_pass_f32(usp_solver* s, int
     t.st = s->st;
     t.tw = s->tw32;
     t.sym = s->symf;
+    t.bt = c.bt;
     const int grid = (int)std::min<int64_t>(t.tiles, s->num_sms);
     const CUtensorMap map = s->map_ax[axis];
     return [=](cudaStream_t st) { return launch_cols_tma(n, map, t, grid, st); };
@@ -253,7 +280,8 @@ static RowsArgs<float> rows_args(usp_solver* s, const float2* y, const float2* x
                                  float2* xout, int flags) {
   RowsArgs<float> r{};
   r.flags = flags | (s->vreal ? F_VREAL : 0);
-  r.nrows = s->N / s->n[s->ndim - 1];
+  r.nrows = s->NB / s->n[s->ndim - 1];
+  r.bt = batch_desc(s, 1);
   r.x_in = xin;
   r.x_out = xout;
   r.y = y;
@@ -315,7 +343,9 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
     const double bytes = 32.0 + vb + (xz ? 0.0 : 8.0);
     // bulk copies read y, V and the scratch field: 16-byte aligned sources
     const bool aligned = (((uintptr_t)y | (uintptr_t)s->V | (uintptr_t)s->buf) & 15u) == 0;
-    if (!s->opt.no_tma && aligned && (nx == 128 || nx == 256)) {
+    const int64_t tile_rows = nx == 256 ? 32 : 64;
+    const bool tiles_fit = s->B == 1 || (r.bt.rows_per % tile_rows) == 0;
+    if (!s->opt.no_tma && aligned && tiles_fit && (nx == 128 || nx == 256)) {
       RowsTmaArgs t{};
       t.flags = r.flags;
       t.nrows = r.nrows;
@@ -329,7 +359,8 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
       t.st = s->st;
       t.hist = s->hist;
       t.alpha = (float)s->alpha;
-      const int64_t tiles = (r.nrows + (nx == 256 ? 32 : 64) - 1) / (nx == 256 ? 32 : 64);
+      t.bt = r.bt;
+      const int64_t tiles = (r.nrows + tile_rows - 1) / tile_rows;
       const int tgrid = (int)std::min<int64_t>(tiles, s->num_sms);
       P.push_back({"rows_inv_post_pre_fwd", bytes,
                    [=](cudaStream_t st) { return launch_rows_tma(nx, t, tgrid, st); }});
@@ -345,7 +376,7 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
 // ---- fused two-pass schedule (grids nz x 256 x 256, fused3d_kernels.cu)
 
 static bool fused_supported(const usp_solver* s) {
-  return s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256 && s->plane_clusters > 0 &&
+  return s->B == 1 && s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256 && s->plane_clusters > 0 &&
          s->maps_ok;
 }
 // Automatic choice: the pencil schedule; schedule 2 selects the fused one
@@ -437,13 +468,14 @@ static cudaError_t enqueue_iteration(usp_solver* s, const float2* y, const float
 // r = y - A x (or A x with apply_a) in FP64; norms into s->red[0..1].
 static usp_status enqueue_residual64(usp_solver* s, const float2* x, const float2* y, float2* rout,
                                      bool apply_a) {
-  if (!s->buf64) CUDA_TRY(cudaMalloc(&s->buf64, sizeof(double2) * s->N));
+  if (!s->buf64) CUDA_TRY(cudaMalloc(&s->buf64, sizeof(double2) * s->NB));
   const int vflag = s->vreal ? F_VREAL : 0;
   const int nd = s->ndim;
   const int nx = s->n[nd - 1];
   RowsArgs<double> r{};
   r.flags = F_NOSTATE | vflag | (apply_a ? F_APPLY_A : 0);
-  r.nrows = s->N / nx;
+  r.nrows = s->NB / nx;
+  r.bt = batch_desc(s, 1);
   r.x_in = x;
   r.y = y;
   r.V = s->V;
@@ -474,7 +506,8 @@ static usp_status enqueue_residual64(usp_solver* s, const float2* x, const float
     r.mode = R_IN_BUF | R_INV | R_OUT_RESID;
     CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
   }
-  CUDA_TRY(launch_sum_pairs(s->partials, (int)grid, s->red, s->stream));
+  // per-problem sums of the block partials (blocks never straddle problems)
+  CUDA_TRY(launch_sum_pairs(s->partials, (int)(grid / s->B), s->B, s->red, s->stream));
   g_launches.fetch_add(nd == 1 ? 2 : (nd == 2 ? 4 : 6));
   return USP_OK;
 }
@@ -501,18 +534,26 @@ static void destroy_impl(usp_solver* s) {
   cudaFree(s->buf64);
   cudaFree(s->hy);
   cudaFree(s->hx);
+  cudaFree(s->bsym32);
+  cudaFree(s->bsym64);
+  cudaFree(s->balpha);
+  cudaFree(s->bmask);
+  cudaFreeHost(s->bmask_host);
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream) cudaStreamDestroy(s->stream);
   cudaSetDevice(cur);
   delete s;
 }
 
-extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol* lsym,
-                                        const void* V, int32_t V_is_real, double alpha,
-                                        void* cuda_stream, usp_solver** out) {
+// Create a solver for `count` independent problems on one grid (count == 1:
+// the single-problem solver).  lsyms, alphas: host arrays of `count`.
+static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol* lsyms,
+                              const void* V, int32_t V_is_real, const double* alphas,
+                              void* cuda_stream, usp_solver** out) {
   if (!out) return fail(USP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (!grid || !lsym || !V) return fail(USP_ERR_INVALID_ARG, "grid, lsym and V must be non-NULL");
+  if (!grid || !lsyms || !V || !alphas) return fail(USP_ERR_INVALID_ARG, "grid, lsym and V must be non-NULL");
+  if (count < 1) return fail(USP_ERR_INVALID_ARG, "batch count must be >= 1 (got %d)", count);
   if (grid->ndim < 1 || grid->ndim > 3)
     return fail(USP_ERR_INVALID_ARG, "ndim must be 1, 2 or 3 (got %d)", grid->ndim);
   if (!(grid->dx > 0.0) || !std::isfinite(grid->dx))
@@ -525,29 +566,45 @@ extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol*
                   ax, (long long)grid->n[ax]);
     N *= grid->n[ax];
   }
-  const double sv[4] = {lsym->a_re, lsym->a_im, lsym->b_re, lsym->b_im};
-  for (double v : sv)
-    if (!std::isfinite(v)) return fail(USP_ERR_INVALID_ARG, "symbol coefficients must be finite");
-  // Re(Lhat(p) + 1) > 0 on the grid: linear in |p|^2 in [0, ndim (pi/dx)^2].
-  const double p2max = grid->ndim * (M_PI / grid->dx) * (M_PI / grid->dx);
-  const double re0 = lsym->b_re + 1.0, re1 = lsym->a_re * p2max + lsym->b_re + 1.0;
-  if (!(re0 > 0.0) || !(re1 > 0.0))
-    return fail(USP_ERR_NOT_ACCRETIVE, "Re(Lhat(p)+1) <= 0 on the grid (%.3g at p=0, %.3g at |p|max)", re0, re1);
-  if (std::isnan(alpha) || std::isinf(alpha) || alpha > 2.0)
-    return fail(USP_ERR_ALPHA_RANGE, "alpha must be finite and in (0, 2] (or <= 0 for automatic)");
+  for (int p = 0; p < count; ++p) {
+    const usp_lsymbol* lsym = lsyms + p;
+    const double sv[4] = {lsym->a_re, lsym->a_im, lsym->b_re, lsym->b_im};
+    for (double v : sv)
+      if (!std::isfinite(v)) return fail(USP_ERR_INVALID_ARG, "symbol coefficients must be finite (problem %d)", p);
+    // Re(Lhat(p) + 1) > 0 on the grid: linear in |p|^2 in [0, ndim (pi/dx)^2].
+    const double p2max = grid->ndim * (M_PI / grid->dx) * (M_PI / grid->dx);
+    const double re0 = lsym->b_re + 1.0, re1 = lsym->a_re * p2max + lsym->b_re + 1.0;
+    if (!(re0 > 0.0) || !(re1 > 0.0))
+      return fail(USP_ERR_NOT_ACCRETIVE, "Re(Lhat(p)+1) <= 0 on the grid (%.3g at p=0, %.3g at |p|max; problem %d)",
+                  re0, re1, p);
+    if (std::isnan(alphas[p]) || std::isinf(alphas[p]) || alphas[p] > 2.0)
+      return fail(USP_ERR_ALPHA_RANGE, "alpha must be finite and in (0, 2] (or <= 0 for automatic)");
+  }
+  if (count > 1) {
+    // every block of the rows passes must hold rows of one problem
+    const int nx = (int)grid->n[grid->ndim - 1];
+    const int64_t rows_per = N / nx;
+    const int64_t need = std::max<int64_t>(rows_per_block_f32(nx), rows_per_block_f64(nx));
+    if (grid->ndim < 2 || rows_per % need != 0)
+      return fail(USP_ERR_UNSUPPORTED_SIZE,
+                  "a batch needs a 2-D or 3-D grid with a multiple of %lld lines per problem", (long long)need);
+  }
   usp_status st0 = ensure_device_init();
   if (st0 != USP_OK) return st0;
 
   usp_solver* s = new usp_solver();
+  s->B = count;
   s->ndim = grid->ndim;
   for (int ax = 0; ax < 3; ++ax) s->n[ax] = ax < grid->ndim ? (int)grid->n[ax] : 1;
   s->N = N;
+  s->NB = N * count;
   s->dx = grid->dx;
-  s->sym = *lsym;
+  s->sym = lsyms[0];
   s->vreal = V_is_real != 0;
   s->user_stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&s->device);
-  // symbol in both precisions
+  // symbol in both precisions (problem 0; batches use the per-problem arrays)
+  const usp_lsymbol* lsym = lsyms;
   s->symd.a_re = lsym->a_re; s->symd.a_im = lsym->a_im;
   s->symd.b_re = lsym->b_re; s->symd.b_im = lsym->b_im;
   s->symd.inv_n = 1.0 / (double)N;
@@ -575,48 +632,94 @@ extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol*
     }                                                                              \
   } while (0)
 
+  const int64_t NB = s->NB;
   CREATE_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
   CREATE_TRY(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
-  const size_t vbytes = (s->vreal ? sizeof(float) : sizeof(float2)) * (size_t)N;
+  const size_t esz = s->vreal ? sizeof(float) : sizeof(float2);
+  const size_t vbytes = esz * (size_t)NB;
   CREATE_TRY(cudaMalloc(&s->V, vbytes));
-  CREATE_TRY(cudaMalloc(&s->buf, sizeof(float2) * (size_t)N));
+  CREATE_TRY(cudaMalloc(&s->buf, sizeof(float2) * (size_t)NB));
   const int64_t g32 = rows_grid_f32(s), g64 = rows_grid_f64(s);
-  s->npartials = std::max<int64_t>({g32, 2 * g64, 3 * 1024, 64});
+  // one per block of the rows passes, two per FP64 block, one per 32-line
+  // tile of the staged rows pass, three per statistics block
+  s->npartials = std::max<int64_t>({g32, 2 * g64, NB / s->n[s->ndim - 1] / 32 + 1, 3 * 1024, 64});
   CREATE_TRY(cudaMalloc(&s->partials, sizeof(double) * s->npartials));
-  CREATE_TRY(cudaMalloc(&s->st, sizeof(DevState)));
-  CREATE_TRY(cudaMallocHost(&s->st_host, sizeof(DevState)));
-  CREATE_TRY(cudaMalloc(&s->red, 4 * sizeof(double)));
-  CREATE_TRY(cudaMallocHost(&s->red_host, 4 * sizeof(double)));
-  CREATE_TRY(cudaMemsetAsync(s->st, 0, sizeof(DevState), s->stream));
+  CREATE_TRY(cudaMalloc(&s->st, sizeof(DevState) * count));
+  CREATE_TRY(cudaMallocHost(&s->st_host, sizeof(DevState) * count));
+  const size_t nred = std::max<size_t>(4, 2 * (size_t)count);
+  CREATE_TRY(cudaMalloc(&s->red, nred * sizeof(double)));
+  CREATE_TRY(cudaMallocHost(&s->red_host, nred * sizeof(double)));
+  CREATE_TRY(cudaMemsetAsync(s->st, 0, sizeof(DevState) * count, s->stream));
+  s->histories.assign(count, std::vector<double>());
 
-  // copy V (ordered after the caller's queued work), then its statistics
+  // copy V (ordered after the caller's queued work), then per-problem statistics
   CREATE_TRY(cudaEventRecord(s->ev, s->user_stream));
   CREATE_TRY(cudaStreamWaitEvent(s->stream, s->ev, 0));
   CREATE_TRY(launch_copy_bytes(s->V, V, vbytes, s->stream));
-  int nb = (int)std::min<int64_t>(1024, (N + 255) / 256);
-  CREATE_TRY(launch_v_stats(s->V, s->vreal, N, s->partials, nb, s->red, s->stream));
-  g_launches.fetch_add(2);
-  CREATE_TRY(cudaMemcpyAsync(s->red_host, s->red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  CREATE_TRY(cudaStreamSynchronize(s->stream));
-  const double vmax = s->red_host[0], astar = s->red_host[1], bad = s->red_host[2];
-  if (bad > 0) {
-    destroy_impl(s);
-    return fail(USP_ERR_NONFINITE, "V holds %.0f non-finite values", bad);
+  const int nb = (int)std::min<int64_t>(1024, (N + 255) / 256);
+  s->alphas.assign(count, 0.0);
+  for (int p = 0; p < count; ++p) {
+    const void* Vp = static_cast<const char*>(s->V) + esz * (size_t)N * p;
+    CREATE_TRY(launch_v_stats(Vp, s->vreal, N, s->partials, nb, s->red, s->stream));
+    g_launches.fetch_add(2);
+    CREATE_TRY(cudaMemcpyAsync(s->red_host, s->red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CREATE_TRY(cudaStreamSynchronize(s->stream));
+    const double vmax = s->red_host[0], astar = s->red_host[1], bad = s->red_host[2];
+    if (bad > 0) {
+      destroy_impl(s);
+      return fail(USP_ERR_NONFINITE, "V holds %.0f non-finite values (problem %d)", bad, p);
+    }
+    if (!(vmax < 1.0)) {
+      destroy_impl(s);
+      return fail(USP_ERR_V_NOT_CONTRACTIVE, "max|V| = %.6g >= 1 (problem %d)", vmax, p);
+    }
+    s->vmax = std::max(s->vmax, vmax);
+    s->alphas[p] = alphas[p] > 0.0 ? alphas[p] : astar;
   }
-  if (!(vmax < 1.0)) {
-    destroy_impl(s);
-    return fail(USP_ERR_V_NOT_CONTRACTIVE, "max|V| = %.6g >= 1", vmax);
+  s->alpha = s->alphas[0];
+  if (count > 1) {
+    std::vector<float4> h32(count);
+    std::vector<double> h64(4 * (size_t)count);
+    std::vector<float> ha(count);
+    for (int p = 0; p < count; ++p) {
+      h32[p] = make_float4((float)lsyms[p].a_re, (float)lsyms[p].a_im, (float)lsyms[p].b_re,
+                           (float)lsyms[p].b_im);
+      h64[4 * p] = lsyms[p].a_re;
+      h64[4 * p + 1] = lsyms[p].a_im;
+      h64[4 * p + 2] = lsyms[p].b_re;
+      h64[4 * p + 3] = lsyms[p].b_im;
+      ha[p] = (float)s->alphas[p];
+    }
+    CREATE_TRY(cudaMalloc(&s->bsym32, sizeof(float4) * count));
+    CREATE_TRY(cudaMalloc(&s->bsym64, sizeof(double) * 4 * count));
+    CREATE_TRY(cudaMalloc(&s->balpha, sizeof(float) * count));
+    CREATE_TRY(cudaMalloc(&s->bmask, sizeof(int) * count));
+    CREATE_TRY(cudaMallocHost(&s->bmask_host, sizeof(int) * count));
+    CREATE_TRY(cudaMemcpy(s->bsym32, h32.data(), sizeof(float4) * count, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(s->bsym64, h64.data(), sizeof(double) * 4 * count, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(s->balpha, ha.data(), sizeof(float) * count, cudaMemcpyHostToDevice));
   }
-  s->vmax = vmax;
-  s->alpha = alpha > 0.0 ? alpha : astar;
   s->tw32 = twiddle_table_f32();
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   if (s->num_sms < 1) s->num_sms = 1;
   build_maps(s);
-  if (s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256) s->plane_clusters = plane_max_active_clusters();
+  if (count == 1 && s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256)
+    s->plane_clusters = plane_max_active_clusters();
   *out = s;
   return USP_OK;
 #undef CREATE_TRY
+}
+
+extern "C" usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol* lsym,
+                                        const void* V, int32_t V_is_real, double alpha,
+                                        void* cuda_stream, usp_solver** out) {
+  return create_impl(grid, 1, lsym, V, V_is_real, &alpha, cuda_stream, out);
+}
+
+extern "C" usp_status usp_batch_create(const usp_grid* grid, int32_t count,
+                                       const usp_lsymbol* lsyms, const void* V, int32_t V_is_real,
+                                       const double* alphas, void* cuda_stream, usp_solver** out) {
+  return create_impl(grid, count, lsyms, V, V_is_real, alphas, cuda_stream, out);
 }
 
 extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* opt) {
@@ -645,7 +748,7 @@ static usp_status ensure_hist(usp_solver* s, int cap) {
   cudaFree(s->hist);
   s->hist = nullptr;
   s->hist_cap = 0;
-  CUDA_TRY(cudaMalloc(&s->hist, sizeof(double) * (size_t)cap));
+  CUDA_TRY(cudaMalloc(&s->hist, sizeof(double) * (size_t)cap * s->B));
   s->hist_cap = cap;
   free_graphs(s);  // graphs captured the old pointer
   return USP_OK;
@@ -680,16 +783,16 @@ static usp_status get_graph(usp_solver* s, const float2* y, float2* x, int chunk
 }
 
 static usp_status read_state(usp_solver* s) {
-  CUDA_TRY(cudaMemcpyAsync(s->st_host, s->st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->st_host, s->st, sizeof(DevState) * s->B, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   return USP_OK;
 }
 static usp_status write_state(usp_solver* s) {
-  CUDA_TRY(cudaMemcpyAsync(s->st, s->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->st, s->st_host, sizeof(DevState) * s->B, cudaMemcpyHostToDevice, s->stream));
   return USP_OK;
 }
 
-// Run iterations on (y, x) until the device state says done.
+// Run iterations on (y, x) until every problem's device state says done.
 static usp_status run_phase(usp_solver* s, const float2* y, float2* x, bool zero_start) {
   const int chunk = s->opt.chunk > 0 ? s->opt.chunk : 8;
   // the first iteration is launched directly (it may start from x = 0)
@@ -701,127 +804,210 @@ static usp_status run_phase(usp_solver* s, const float2* y, float2* x, bool zero
   cudaGraphExec_t ge = nullptr;
   usp_status st = get_graph(s, y, x, chunk, &ge);
   if (st != USP_OK) return st;
+  const int B = s->B;
   int launches = 1;
-  int prev_it = 0;
-  double prev_r = 0.0;
-  // Every launched iteration either counts in `it` or finds done set, so
-  // more launched iterations than the remaining budget (plus a chunk of
-  // slack) means the device state machine is broken: stop, do not spin.
-  const int start_it = s->st_host->it;
-  const int64_t budget = (int64_t)(s->st_host->it_limit - start_it) + 2 * chunk + 1;
+  std::vector<int> prev_it(B, 0);
+  std::vector<double> prev_r(B, 0.0);
+  // Every launched iteration either counts in a running problem's `it` or
+  // finds it done, so more launched iterations than the largest remaining
+  // budget (plus a chunk of slack) means the device state machine is
+  // broken: stop, do not spin.
+  int64_t budget = 0;
+  for (int p = 0; p < B; ++p)
+    if (!s->st_host[p].done)
+      budget = std::max<int64_t>(budget, (int64_t)s->st_host[p].it_limit - s->st_host[p].it);
+  budget += 2 * chunk + 1;
   int64_t launched = 1;
   for (;;) {
     for (int k = 0; k < launches; ++k) CUDA_TRY(cudaGraphLaunch(ge, s->stream));
     launched += (int64_t)launches * chunk;
     g_launches.fetch_add((int64_t)launches * chunk * passes_per_it);
     if ((st = read_state(s)) != USP_OK) return st;
-    const DevState& h = *s->st_host;
-    if (h.done) return USP_OK;
-    if (launched > budget)
-      return fail(USP_ERR_CUDA, "device iteration state did not stop (it=%d of %d)", h.it, h.it_limit);
-    // Estimate the iterations left from the observed contraction rate and
-    // size the next group of launches to overshoot by at most one chunk.
-    int want = 4 * launches;
-    if (prev_it > 0 && h.it > prev_it && h.last_r > 0 && prev_r > h.last_r) {
-      const double rate = std::pow(h.last_r / prev_r, 1.0 / (h.it - prev_it));
-      const double left = std::log(std::max(h.tol, 1e-300) / h.last_r) / std::log(rate);
-      want = (int)std::ceil(std::max(1.0, left) / chunk);
+    bool all_done = true;
+    int want = 1, left_max = 1;
+    for (int p = 0; p < B; ++p) {
+      const DevState& h = s->st_host[p];
+      if (h.done) continue;
+      all_done = false;
+      // Estimate the iterations left from the observed contraction rate and
+      // size the next group of launches (slowest problem) to overshoot by at
+      // most one chunk.
+      int w = 4 * launches;
+      if (prev_it[p] > 0 && h.it > prev_it[p] && h.last_r > 0 && prev_r[p] > h.last_r) {
+        const double rate = std::pow(h.last_r / prev_r[p], 1.0 / (h.it - prev_it[p]));
+        const double left = std::log(std::max(h.tol, 1e-300) / h.last_r) / std::log(rate);
+        w = (int)std::ceil(std::max(1.0, left) / chunk);
+      }
+      want = std::max(want, w);
+      left_max = std::max(left_max, h.it_limit - h.it);
+      prev_it[p] = h.it;
+      prev_r[p] = h.last_r;
     }
-    prev_it = h.it;
-    prev_r = h.last_r;
+    if (all_done) return USP_OK;
+    if (launched > budget) {
+      const DevState& h = s->st_host[0];
+      return fail(USP_ERR_CUDA, "device iteration state did not stop (it=%d of %d)", h.it, h.it_limit);
+    }
     launches = std::min(std::max(want, 1), std::max(1, 512 / chunk));
-    const int left_it = h.it_limit - h.it;
-    launches = std::min(launches, std::max(1, (left_it + chunk - 1) / chunk));
+    launches = std::min(launches, std::max(1, (left_max + chunk - 1) / chunk));
   }
 }
 
+static bool converged_state(const DevState& h, double tol) {
+  return (h.status != ST_NONFINITE && h.status != ST_DIVERGED && h.status != ST_TIMEOUT) &&
+         (h.it > 0 || h.ref == 0.0) && (h.last_r < tol || h.ref == 0.0);
+}
+
+// Status and message of one finished problem (prefix names it in a batch).
+static usp_status problem_status(const DevState& h, double tol, bool stagnated, const char* prefix) {
+  if (h.status == ST_TIMEOUT) return fail(USP_ERR_CUDA, "%sa bounded wait for the copy engine timed out", prefix);
+  if (h.status == ST_NONFINITE) return fail(USP_ERR_NONFINITE, "%snon-finite value in y, x0 or an iterate", prefix);
+  if (h.status == ST_DIVERGED)
+    return fail(USP_ERR_DIVERGED, "%s||Delta|| grew from %.3g to %.3g (relative)", prefix, h.phase_first_r,
+                h.last_r);
+  if (!converged_state(h, tol))
+    return fail(USP_ERR_NOT_CONVERGED, "%s%s after %d iterations, residual %.3g", prefix,
+                stagnated ? "stagnated" : "iteration limit reached", h.it, h.last_r);
+  return USP_OK;
+}
+
+// Solve all problems of the solver (one, or a batch sharing the passes).
+// ref_norms: per problem (<= 0: automatic), or nullptr; outs, statuses: per
+// problem, or nullptr.
 static usp_status solve_impl(usp_solver* s, const float2* y, float2* x, int use_x0, double tol,
-                             int maxit, double ref_norm, usp_result* out) {
+                             int maxit, const double* ref_norms, usp_result* outs,
+                             usp_status* statuses) {
   usp_status st;
   if ((st = ensure_hist(s, maxit)) != USP_OK) return st;
+  const int B = s->B;
   const bool refine = s->opt.plain == 0;
   const int max_ref = s->opt.max_refinements > 0 ? s->opt.max_refinements : 4;
 
-  DevState& h = *s->st_host;
-  std::memset(&h, 0, sizeof h);
-  h.it_limit = maxit;
-  h.ref = ref_norm > 0 ? ref_norm : 0.0;
-  h.tol = tol;
-  if ((st = write_state(s)) != USP_OK) return st;
-
-  int refinements = 0;
-  bool stagnated = false;
-  bool skip = false;
-  if (use_x0 && !(ref_norm > 0)) {
-    // ||B (L+I)^-1 y||: Delta at x = 0, no update (Algorithm 1's denominator)
+  bool need_ref = false;
+  for (int p = 0; p < B; ++p) {
+    DevState& h = s->st_host[p];
+    std::memset(&h, 0, sizeof h);
+    h.it_limit = maxit;
+    const double rn = ref_norms ? ref_norms[p] : 0.0;
+    h.ref = rn > 0 ? rn : 0.0;
+    h.tol = tol;
+    need_ref = need_ref || !(rn > 0);
+  }
+  std::vector<int> refinements(B, 0), active(B, 1);
+  std::vector<char> stagnated(B, 0);
+  if (use_x0 && need_ref) {
+    // ||B (L+I)^-1 y||: Delta at x = 0, no update (Algorithm 1's
+    // denominator), for the problems without a given reference norm
+    for (int p = 0; p < B; ++p) s->st_host[p].done = s->st_host[p].ref > 0 ? 1 : 0;
+    if ((st = write_state(s)) != USP_OK) return st;
     cudaError_t e = enqueue_iteration(s, y, x, x, F_XZERO | F_REF, s->stream, true, true);
     if (e != cudaSuccess) return fail(USP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     if ((st = read_state(s)) != USP_OK) return st;
-    skip = h.done != 0;  // non-finite y
+    for (int p = 0; p < B; ++p) {
+      DevState& h = s->st_host[p];
+      const double rn = ref_norms ? ref_norms[p] : 0.0;
+      if (rn > 0) h.done = 0;
+      else if (h.done) active[p] = 0;  // non-finite y
+    }
   }
 
   const float2* cy = y;  // source of the current phase
   float2* cx = x;        // unknown of the current phase (x, then the correction z)
   bool zero_start = !use_x0;
-  while (!skip && h.it < maxit) {
-    const bool can_refine = refine && refinements < max_ref;
-    h.done = 0;
-    h.status = ST_RUNNING;
-    h.phase_start = h.it;
-    h.tol = (can_refine && refinements == 0) ? 8.0 * tol : tol;
-    h.stall_window = can_refine ? 64 : 0;
+  std::vector<char> can_refine(B, 0);
+  for (;;) {
+    bool any = false;
+    for (int p = 0; p < B; ++p) {
+      DevState& h = s->st_host[p];
+      if (!active[p] || h.it >= maxit) {
+        active[p] = 0;
+        h.done = 1;
+        continue;
+      }
+      any = true;
+      can_refine[p] = refine && refinements[p] < max_ref;
+      h.done = 0;
+      h.status = ST_RUNNING;
+      h.phase_start = h.it;
+      h.tol = (can_refine[p] && refinements[p] == 0) ? 8.0 * tol : tol;
+      h.stall_window = can_refine[p] ? 64 : 0;
+    }
+    if (!any) break;
     if ((st = write_state(s)) != USP_OK) return st;
     if ((st = run_phase(s, cy, cx, zero_start)) != USP_OK) return st;
     if (cx != x) {
-      CUDA_TRY(launch_axpy1(x, cx, s->N, s->stream));  // x = x_b + z
+      // x = x_b + z for the problems of this phase
+      if (B > 1) {
+        for (int p = 0; p < B; ++p) s->bmask_host[p] = active[p];
+        CUDA_TRY(cudaMemcpyAsync(s->bmask, s->bmask_host, sizeof(int) * B, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(launch_axpy1(x, cx, s->NB, s->stream, s->bmask, s->N));
+      } else {
+        CUDA_TRY(launch_axpy1(x, cx, s->NB, s->stream));
+      }
       g_launches.fetch_add(1);
     }
-    const int stt = h.status;
-    stagnated = (stt == ST_STAGNATED);
-    if (stt == ST_NONFINITE || stt == ST_DIVERGED || stt == ST_MAXIT || stt == ST_TIMEOUT) break;
-    if (h.last_r < tol || h.ref == 0.0) break;  // converged
-    if (!can_refine) break;
+    bool again = false;
+    for (int p = 0; p < B; ++p) {
+      if (!active[p]) continue;
+      const DevState& h = s->st_host[p];
+      const int stt = h.status;
+      stagnated[p] = (stt == ST_STAGNATED);
+      const bool terminal = stt == ST_NONFINITE || stt == ST_DIVERGED || stt == ST_MAXIT ||
+                            stt == ST_TIMEOUT || h.last_r < tol || h.ref == 0.0 || !can_refine[p];
+      if (terminal) active[p] = 0;
+      else again = true;
+    }
+    if (!again) break;
     // Refinement: Delta(x_b + z; y) = Delta(z; y - A x_b) exactly because
     // A + B = L + I, so the same FP32 iteration continues on z with the
     // source y - A x_b formed in FP64.
-    if (!s->z) CUDA_TRY(cudaMalloc(&s->z, sizeof(float2) * s->N));
-    if (!s->yp) CUDA_TRY(cudaMalloc(&s->yp, sizeof(float2) * s->N));
+    if (!s->z) CUDA_TRY(cudaMalloc(&s->z, sizeof(float2) * s->NB));
+    if (!s->yp) CUDA_TRY(cudaMalloc(&s->yp, sizeof(float2) * s->NB));
     if ((st = enqueue_residual64(s, x, y, s->yp, false)) != USP_OK) return st;
-    ++refinements;
+    for (int p = 0; p < B; ++p)
+      if (active[p]) ++refinements[p];
     cy = s->yp;
     cx = s->z;
     zero_start = true;
   }
   if ((st = read_state(s)) != USP_OK) return st;
 
-  const int nit = std::min(h.it, s->hist_cap);
-  s->history.assign(nit, 0.0);
-  if (nit > 0) CUDA_TRY(cudaMemcpy(s->history.data(), s->hist, sizeof(double) * nit, cudaMemcpyDeviceToHost));
-
-  const bool converged = (h.status != ST_NONFINITE && h.status != ST_DIVERGED &&
-                          h.status != ST_TIMEOUT) &&
-                         (h.it > 0 || h.ref == 0.0) && (h.last_r < tol || h.ref == 0.0);
-  if (out) {
-    out->iterations = h.it;
-    out->converged = converged ? 1 : 0;
-    out->refinements = refinements;
-    out->stagnated = stagnated ? 1 : 0;
-    out->final_rel_residual = h.last_r;
-    out->ref_norm = h.ref;
-    out->alpha = s->alpha;
+  usp_status first_bad = USP_OK;
+  std::string first_msg;
+  for (int p = 0; p < B; ++p) {
+    const DevState& h = s->st_host[p];
+    const int nit = std::min(h.it, s->hist_cap);
+    s->histories[p].assign(nit, 0.0);
+    if (nit > 0)
+      CUDA_TRY(cudaMemcpy(s->histories[p].data(), s->hist + (size_t)p * s->hist_cap, sizeof(double) * nit,
+                          cudaMemcpyDeviceToHost));
+    if (outs) {
+      usp_result& o = outs[p];
+      o.iterations = h.it;
+      o.converged = converged_state(h, tol) ? 1 : 0;
+      o.refinements = refinements[p];
+      o.stagnated = stagnated[p] ? 1 : 0;
+      o.final_rel_residual = h.last_r;
+      o.ref_norm = h.ref;
+      o.alpha = s->alphas[p];
+    }
+    char prefix[48] = "";
+    if (B > 1) std::snprintf(prefix, sizeof prefix, "problem %d: ", p);
+    const usp_status ps = problem_status(h, tol, stagnated[p] != 0, prefix);
+    if (statuses) statuses[p] = ps;
+    if (ps != USP_OK && first_bad == USP_OK) {
+      first_bad = ps;
+      first_msg = g_last_error;
+    }
   }
-  if (h.status == ST_TIMEOUT) return fail(USP_ERR_CUDA, "a bounded wait for the copy engine timed out");
-  if (h.status == ST_NONFINITE) return fail(USP_ERR_NONFINITE, "non-finite value in y, x0 or an iterate");
-  if (h.status == ST_DIVERGED)
-    return fail(USP_ERR_DIVERGED, "||Delta|| grew from %.3g to %.3g (relative)", h.phase_first_r, h.last_r);
-  if (!converged)
-    return fail(USP_ERR_NOT_CONVERGED, "%s after %d iterations, residual %.3g",
-                stagnated ? "stagnated" : "iteration limit reached", h.it, h.last_r);
-  return USP_OK;
+  s->history = s->histories[0];
+  if (first_bad != USP_OK) g_last_error = first_msg;
+  return first_bad;
 }
 
 static usp_status check_solve_args(usp_solver* s, const void* y, void* x, double tol, int maxit) {
   if (!s) return fail(USP_ERR_INVALID_ARG, "solver is NULL");
+  if (s->B > 1 && !(y && x)) return fail(USP_ERR_INVALID_ARG, "y and x must be non-NULL");
   if (!y || !x) return fail(USP_ERR_INVALID_ARG, "y and x must be non-NULL");
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(USP_ERR_INVALID_ARG, "tol must be finite and >= 0");
   if (maxit < 1) return fail(USP_ERR_INVALID_ARG, "maxit must be >= 1");
@@ -832,6 +1018,7 @@ extern "C" usp_status usp_solve(usp_solver* s, const void* y, void* x, int32_t u
                                 int32_t maxit, double ref_norm, usp_result* out) {
   usp_status st = check_solve_args(s, y, x, tol, maxit);
   if (st != USP_OK) return st;
+  if (s->B > 1) return fail(USP_ERR_INVALID_ARG, "a batch solver is solved with usp_batch_solve");
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
@@ -840,10 +1027,42 @@ extern "C" usp_status usp_solve(usp_solver* s, const void* y, void* x, int32_t u
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev, 0);
   if (e != cudaSuccess) st = fail(USP_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
   if (st == USP_OK)
-    st = solve_impl(s, (const float2*)y, (float2*)x, use_x0, tol, maxit, ref_norm, out);
+    st = solve_impl(s, (const float2*)y, (float2*)x, use_x0, tol, maxit, &ref_norm, out, nullptr);
   cudaStreamSynchronize(s->stream);
   if (cur != s->device) cudaSetDevice(cur);
   return st;
+}
+
+extern "C" usp_status usp_batch_solve(usp_solver* s, const void* y, void* x, int32_t use_x0,
+                                      double tol, int32_t maxit, const double* ref_norms,
+                                      usp_result* results, usp_status* statuses) {
+  usp_status st = check_solve_args(s, y, x, tol, maxit);
+  if (st != USP_OK) return st;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
+  cudaError_t e = cudaEventRecord(s->ev, s->user_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev, 0);
+  if (e != cudaSuccess) st = fail(USP_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
+  if (st == USP_OK)
+    st = solve_impl(s, (const float2*)y, (float2*)x, use_x0, tol, maxit, ref_norms, results, statuses);
+  cudaStreamSynchronize(s->stream);
+  if (cur != s->device) cudaSetDevice(cur);
+  return st;
+}
+
+extern "C" usp_status usp_batch_history(const usp_solver* s, int32_t problem, double* host_out,
+                                        int32_t capacity, int32_t* n_out) {
+  if (!s || !n_out) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  if (problem < 0 || problem >= s->B)
+    return fail(USP_ERR_INVALID_ARG, "problem %d out of range [0, %d)", problem, s->B);
+  if (capacity > 0 && !host_out) return fail(USP_ERR_INVALID_ARG, "host_out is NULL");
+  const std::vector<double>& h = s->histories[problem];
+  const int n = (int)h.size();
+  const int m = std::min(n, std::max(0, (int)capacity));
+  if (m > 0) std::memcpy(host_out, h.data(), sizeof(double) * m);
+  *n_out = n;
+  return USP_OK;
 }
 
 extern "C" usp_status usp_solve_host(usp_solver* s, const void* y_host, void* x_host,
@@ -851,15 +1070,16 @@ extern "C" usp_status usp_solve_host(usp_solver* s, const void* y_host, void* x_
                                      usp_result* out) {
   usp_status st = check_solve_args(s, y_host, x_host, tol, maxit);
   if (st != USP_OK) return st;
+  if (s->B > 1) return fail(USP_ERR_INVALID_ARG, "a batch solver is solved with usp_batch_solve");
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
-  const size_t bytes = sizeof(float2) * (size_t)s->N;
+  const size_t bytes = sizeof(float2) * (size_t)s->NB;
   if (!s->hy) CUDA_TRY(cudaMalloc(&s->hy, bytes));
   if (!s->hx) CUDA_TRY(cudaMalloc(&s->hx, bytes));
   CUDA_TRY(cudaMemcpyAsync(s->hy, y_host, bytes, cudaMemcpyHostToDevice, s->stream));
   if (use_x0) CUDA_TRY(cudaMemcpyAsync(s->hx, x_host, bytes, cudaMemcpyHostToDevice, s->stream));
-  st = solve_impl(s, s->hy, s->hx, use_x0, tol, maxit, ref_norm, out);
+  st = solve_impl(s, s->hy, s->hx, use_x0, tol, maxit, &ref_norm, out, nullptr);
   if (st == USP_OK || st == USP_ERR_NOT_CONVERGED) {
     const std::string keep = g_last_error;
     cudaError_t e = cudaMemcpyAsync(x_host, s->hx, bytes, cudaMemcpyDeviceToHost, s->stream);
@@ -893,12 +1113,17 @@ static usp_status residual_common(usp_solver* s, const void* x, const void* y, v
   usp_status st = (e == cudaSuccess) ? USP_OK : fail(USP_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
   if (st == USP_OK) st = enqueue_residual64(s, (const float2*)x, (const float2*)y, (float2*)r, apply_a);
   if (st == USP_OK) {
-    e = cudaMemcpyAsync(s->red_host, s->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    e = cudaMemcpyAsync(s->red_host, s->red, 2 * sizeof(double) * s->B, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = fail(USP_ERR_CUDA, "residual: %s", cudaGetErrorString(e));
   }
   if (st == USP_OK && rel_out) {
-    const double nr = std::sqrt(s->red_host[0]), ny = std::sqrt(s->red_host[1]);
+    double sr = 0.0, sy = 0.0;  // a batch: over all problems
+    for (int p = 0; p < s->B; ++p) {
+      sr += s->red_host[2 * p];
+      sy += s->red_host[2 * p + 1];
+    }
+    const double nr = std::sqrt(sr), ny = std::sqrt(sy);
     *rel_out = ny > 0 ? nr / ny : nr;
   }
   cudaStreamSynchronize(s->stream);
@@ -950,11 +1175,13 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
   if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
   usp_status st = ensure_hist(s, iters + 1);
   if (st != USP_OK) return st;
-  DevState& h = *s->st_host;
-  std::memset(&h, 0, sizeof h);
-  h.it_limit = iters + 1;
-  h.ref = 1.0;   // fixed denominator: nothing stops the timed iterations
-  h.tol = 0.0;
+  for (int p = 0; p < s->B; ++p) {
+    DevState& h = s->st_host[p];
+    std::memset(&h, 0, sizeof h);
+    h.it_limit = iters + 1;
+    h.ref = 1.0;   // fixed denominator: nothing stops the timed iterations
+    h.tol = 0.0;
+  }
   if ((st = write_state(s)) != USP_OK) return st;
   for (auto& p : prologue_passes(s, (const float2*)y, (const float2*)x, 0)) {
     cudaError_t e = p.go(s->stream);
@@ -992,7 +1219,7 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
       std::strncpy(out[k].name, passes[k].name, sizeof out[k].name - 1);
       out[k].launches = iters;
       out[k].ms = acc[k] / iters;
-      out[k].bytes = passes[k].bytes_per_point * (double)s->N;
+      out[k].bytes = passes[k].bytes_per_point * (double)s->NB;
     }
     *n_out = (int32_t)np;
   }

@@ -166,3 +166,99 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchSolver(Solver):
+    """``count`` independent problems (L_j + V_j) x_j = y_j on one grid, every
+    pass of the iteration run once over all of them, each problem with its
+    own symbol, step, convergence test, history and refinement.
+
+    shape : grid of one problem (2 or 3 axes).
+    a, b  : sequences of ``count`` symbol coefficients.
+    V     : CUDA tensor (count, *shape), complex64 or float32.
+    alpha : scalar or sequence of ``count`` (<= 0: automatic).
+    """
+
+    def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
+                 schedule=0, chunk=0, max_refinements=0, no_tma=False):
+        import torch
+        L = _lib.lib()
+        if not V.is_cuda:
+            raise ValueError("V must be a CUDA tensor")
+        if V.dtype not in (torch.complex64, torch.float32):
+            raise ValueError("V must be complex64 or float32")
+        V = V.contiguous()
+        self.shape = tuple(int(n) for n in shape)
+        self.count = int(V.shape[0])
+        if int(np.prod(self.shape)) * self.count != V.numel():
+            raise ValueError("V has %d elements, %d problems of grid %s"
+                             % (V.numel(), self.count, self.shape))
+        a, b = list(a), list(b)
+        if len(a) != self.count or len(b) != self.count:
+            raise ValueError("need one symbol per problem")
+        alphas = list(alpha) if hasattr(alpha, "__len__") else [alpha] * self.count
+        if len(alphas) != self.count:
+            raise ValueError("need one alpha per problem")
+        self.device = V.device
+        g = Grid()
+        g.ndim = len(self.shape)
+        for i in range(3):
+            g.n[i] = self.shape[i] if i < len(self.shape) else 1
+        g.dx = float(dx)
+        syms = (LSymbol * self.count)(*[
+            LSymbol(complex(aj).real, complex(aj).imag, complex(bj).real, complex(bj).imag)
+            for aj, bj in zip(a, b)])
+        al = (ctypes.c_double * self.count)(*[float(v) for v in alphas])
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self._stream = stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(L.usp_batch_create(ctypes.byref(g), self.count, syms, _ptr(V),
+                                     int(V.dtype == torch.float32), al,
+                                     ctypes.c_void_p(stream), ctypes.byref(h)))
+        self._h = h
+        self.set_options(plain=plain, schedule=schedule, chunk=chunk,
+                         max_refinements=max_refinements, no_tma=no_tma)
+
+    def solve(self, y, x=None, tol=1e-6, maxit=10000, ref_norms=None, use_x0=False,
+              allow_failed=True):
+        """Solve all problems; returns (x, list of per-problem result dicts,
+        each with its own "status").  With allow_failed, a problem that did
+        not converge, diverged or met a non-finite value is reported in its
+        status instead of raising."""
+        import torch
+        y = y.contiguous()
+        if x is None:
+            x = torch.empty_like(y)
+            use_x0 = False
+        res = (Result * self.count)()
+        sts = (ctypes.c_int32 * self.count)()
+        refs = None
+        if ref_norms is not None:
+            refs = (ctypes.c_double * self.count)(*[float(v) for v in ref_norms])
+        allow = ((_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_DIVERGED, _lib.ERR_NONFINITE)
+                 if allow_failed else (_lib.OK,))
+        with torch.cuda.device(self.device):
+            st = _lib.lib().usp_batch_solve(self._h, _ptr(y), _ptr(x), int(bool(use_x0)),
+                                            float(tol), int(maxit), refs, res, sts)
+        check(st, allow)
+        out = []
+        for j in range(self.count):
+            d = res[j].as_dict()
+            d["status"] = _lib.STATUS[sts[j]]
+            out.append(d)
+        return x, out
+
+    def solve_host(self, *args, **kwargs):
+        raise NotImplementedError("a batch is solved from device tensors (BatchSolver.solve)")
+
+    def history(self, problem=0):
+        n = ctypes.c_int32()
+        check(_lib.lib().usp_batch_history(self._h, int(problem), None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, np.float64)
+        if n.value:
+            check(_lib.lib().usp_batch_history(
+                self._h, int(problem), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                n.value, ctypes.byref(n)))
+        return out

@@ -77,11 +77,39 @@ def test_create_rejects_bad_arguments(L):
     assert "alpha" in _lib.last_error()
 
 
+def _batch_create(L, shape, syms, alphas=None, V=1):
+    g = _grid(shape)
+    count = len(syms)
+    arr = (_lib.LSymbol * max(1, count))(*[_lib.LSymbol(*sy) for sy in syms])
+    al = (ctypes.c_double * max(1, count))(*(alphas or [0.0] * count))
+    h = ctypes.c_void_p()
+    return L.usp_batch_create(ctypes.byref(g), count, arr, ctypes.c_void_p(V), 0, al, None,
+                              ctypes.byref(h))
+
+
+def test_batch_create_rejects_bad_arguments(L):
+    good = (0.0, 0.3, 0.2, -0.5)
+    assert _batch_create(L, (64, 64), []) == _lib.ERR_INVALID_ARG           # count 0
+    assert _batch_create(L, (64, 64), [good, good], V=0) == _lib.ERR_INVALID_ARG
+    # every problem's symbol is validated (Corollary: Re[L+I] > 0)
+    bad = (0.0, 1.0, -1.5, 0.0)
+    assert _batch_create(L, (64, 64), [good, good, bad]) == _lib.ERR_NOT_ACCRETIVE
+    assert "problem 2" in _lib.last_error()
+    assert _batch_create(L, (64, 64), [good, good], alphas=[0.5, 3.0]) == _lib.ERR_ALPHA_RANGE
+    # a batch needs whole blocks of lines per problem: 1-D and thin grids are refused
+    assert _batch_create(L, (256,), [good, good]) == _lib.ERR_UNSUPPORTED_SIZE
+    assert _batch_create(L, (8, 256), [good, good]) == _lib.ERR_UNSUPPORTED_SIZE
+    assert _batch_create(L, (4, 4), [good, good]) == _lib.ERR_UNSUPPORTED_SIZE
+
+
 def test_null_handles(L):
     r = _lib.Result()
     assert L.usp_solve(None, None, None, 0, 1e-6, 10, 0.0, ctypes.byref(r)) == _lib.ERR_INVALID_ARG
     n = ctypes.c_int32()
     assert L.usp_residual_history(None, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID_ARG
+    assert L.usp_batch_history(None, 0, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID_ARG
+    assert L.usp_batch_solve(None, None, None, 0, 1e-6, 10, None, None,
+                             None) == _lib.ERR_INVALID_ARG
     L.usp_solver_destroy(None)
 
 
