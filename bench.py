@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--batch", type=int, default=64,
                    help="problems of the batched leg (2-D 128x128 media; 0 skips it)")
     p.add_argument("--batch-n", type=int, default=128)
+    p.add_argument("--mixed", type=int, default=512,
+                   help="problems of the mixed-size 2-D batch leg (0 skips it)")
     return p.parse_args()
 
 
@@ -350,9 +352,106 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
                         "min_rel_residual": float(h.min()), "argmin": int(h.argmin()) + 1,
                         "iter_per_s": r["iterations"] / dt,
                         "s_to_min_residual": dt * (int(h.argmin()) + 1) / r["iterations"]}
+    out["library_comparator"] = cufft_leg(torch, dev, cf, V, y, shape)
     if args.batch > 0:
         out["batched"] = batched_leg(args, torch, dev)
+    if args.mixed > 0:
+        out["mixed_batch"] = mixed_batch_leg(args, torch, dev)
     return out
+
+
+def mixed_batch_leg(args, torch, dev):
+    """The mixed-size workload: 2-D problems of sides 64-512 (radix 2 and
+    3), Helmholtz and diffusion alternating, each with its own medium; one
+    batch solver per side, autotuned, all sides solved concurrently
+    (usp_solve_many) vs one solver per problem in turn."""
+    from paper_2207_14222_gb300 import canon, inputs
+    from paper_2207_14222_gb300.solver import BatchSolver, Solver, solve_many
+    groups = {}
+    for i in range(args.mixed):
+        prob = inputs.batch_problem(i)
+        cf = canon.canonical(prob)
+        groups.setdefault(prob["S"].shape[0], []).append(cf)
+    sides = sorted(groups)
+    Vg = {n: torch.from_numpy(np.stack([cf["V"].astype(np.complex64) for cf in groups[n]])).to(dev)
+          for n in sides}
+    yg = {n: torch.from_numpy(np.stack([cf["y"] for cf in groups[n]])).to(dev) for n in sides}
+
+    def together():
+        solvers = [BatchSolver((n, n), [cf["a"] for cf in groups[n]],
+                               [cf["b"] for cf in groups[n]], Vg[n]) for n in sides]
+        try:
+            for sv, n in zip(solvers, sides):
+                sv.autotune(yg[n], iters=3)
+            _, res = solve_many(solvers, [yg[n] for n in sides], tol=args.tol,
+                                maxit=args.maxit)
+        finally:
+            for sv in solvers:
+                sv.close()
+        return [r for lst in res for r in lst]
+
+    def one_by_one():
+        res = []
+        for n in sides:
+            for j, cf in enumerate(groups[n]):
+                with Solver((n, n), cf["a"], cf["b"], Vg[n][j]) as sv:
+                    _, r = sv.solve(yg[n][j], tol=args.tol, maxit=args.maxit)
+                res.append(r)
+        return res
+
+    pts = {n: n * n for n in sides}
+    out = {"problems": args.mixed, "tol": args.tol,
+           "sides": {str(n): len(groups[n]) for n in sides},
+           "points": int(sum(pts[n] * len(groups[n]) for n in sides)),
+           "step": "create + autotune + solve every problem to tol + destroy"}
+    for name, fn in (("concurrent_batches", together), ("one_by_one", one_by_one)):
+        fn()  # warm-up (also fills the autotuner's cache)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        its = [r["iterations"] for r in res]
+        out[name] = {"s": dt, "problem_iter_per_s": sum(its) / dt,
+                     "converged": sum(int(r["converged"]) for r in res),
+                     "iterations_min_max": [min(its), max(its)]}
+    out["speedup"] = out["one_by_one"]["s"] / out["concurrent_batches"]["s"]
+    return out
+
+
+def cufft_leg(torch, dev, cf, V, y, shape, iters=20):
+    """The same FP32 iteration written with torch.fft (cuFFT) and torch
+    elementwise ops on the same GPU: the library comparator (not the
+    product path, which runs only the library's own kernels)."""
+    ks = [torch.fft.fftfreq(n, d=cf["dx"], device=dev, dtype=torch.float64) * 2 * np.pi
+          for n in shape]
+    p2 = sum(torch.meshgrid(*[k * k for k in ks], indexing="ij"))
+    a, b = complex(cf["a"]), complex(cf["b"])
+    mult = (1.0 / (a * p2 + b + 1.0)).to(torch.complex64)
+    del p2
+    Bm = (1 - V.to(torch.complex64))
+    alpha = float(np.min(np.real(1.0 / Bm.cpu().numpy())))
+    x = torch.zeros_like(y)
+
+    def it():
+        t = Bm * x + y
+        u = torch.fft.ifftn(torch.fft.fftn(t) * mult)
+        d = Bm * (u - x)
+        x.add_(d, alpha=alpha)
+        return torch.linalg.vector_norm(d)
+
+    for _ in range(3):
+        it()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        it()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    return {"what": "torch.fft (cuFFT) + torch elementwise ops, complex64, same iteration",
+            "iter_per_s": 1e3 / ms, "ms_per_iter": ms}
 
 
 def batched_leg(args, torch, dev):

@@ -42,7 +42,7 @@ extern "C" {
 typedef enum {
   USP_OK = 0,
   USP_ERR_INVALID_ARG = 1,       /* null pointer, bad ndim, tol < 0, ...      */
-  USP_ERR_UNSUPPORTED_SIZE = 2,  /* an axis is not a power of two in [2,256]  */
+  USP_ERR_UNSUPPORTED_SIZE = 2,  /* an axis length is not supported (below)   */
   USP_ERR_V_NOT_CONTRACTIVE = 3, /* max |V| >= 1 (Thm 1 needs ||V|| < 1)      */
   USP_ERR_NOT_ACCRETIVE = 4,     /* Re(Lhat(p) + 1) <= 0 for some p (L+I not
                                     invertible / A + B not accretive,
@@ -59,7 +59,9 @@ typedef enum {
 } usp_status;
 
 /* Grid: ndim in {1,2,3}; n[0..ndim-1] axis lengths, n[ndim-1] fastest;
- * each a power of two in [2, 256].  dx > 0 is the grid spacing (all axes). */
+ * each a power of two in [2, 256], or 96, 192, 384 (3 * 2^k) or 512 (the
+ * transforms add a radix-3 or radix-2 outer stage).  dx > 0 is the grid
+ * spacing (all axes). */
 typedef struct {
   int32_t ndim;
   int64_t n[3];
@@ -169,6 +171,20 @@ usp_status usp_batch_solve(usp_solver* s, const void* y, void* x,
 usp_status usp_batch_history(const usp_solver* s, int32_t problem,
                              double* host_out, int32_t capacity,
                              int32_t* n_out);
+
+/* Solve several solvers (single problems or batches, any grids) at the same
+ * time: one host thread per solver drives that solver's own stream, so their
+ * passes run concurrently on the GPU -- the form for many problems of
+ * different sizes (one batch solver per size).  Each solver runs
+ * usp_batch_solve (Algorithm 1 per problem, automatic reference norms) on
+ * (ys[i], xs[i]) (device pointers, layout as for that solver).  results,
+ * statuses: host arrays over all problems, solver by solver, or NULL.
+ * Returns USP_OK when every problem converged, else the first failing
+ * solver's status and message.  A solver may appear only once. */
+usp_status usp_solve_many(usp_solver* const* solvers, int32_t count,
+                          const void* const* ys, void* const* xs,
+                          int32_t use_x0, double tol, int32_t maxit,
+                          usp_result* results, usp_status* statuses);
 
 /* Replace the options of a solver (host pointer, copied). */
 usp_status usp_solver_set_options(usp_solver* s, const usp_options* opt);
@@ -298,6 +314,17 @@ typedef struct {
  * of kernels per iteration. */
 usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int32_t iters,
                            usp_pass_time* out, int32_t capacity, int32_t* n_out);
+
+/* Autotuner: time one iteration of each pass variant the solver's grid
+ * admits (pencil or fused schedule; TMA-staged or plain-load passes) over
+ * `iters` iterations on (y, x) (device pointers; x is overwritten), keep the
+ * fastest, and size the iterations per CUDA-graph launch (chunk) to about
+ * 0.2 ms of GPU work.  The choice is cached per (grid, batch count, real or
+ * complex V) for the process: a later solver of the same shape takes it
+ * without timing.  Sets the solver's options (plain and max_refinements are
+ * kept) and copies them to *chosen if not NULL. */
+usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_t iters,
+                        usp_options* chosen);
 
 /* Number of kernel launches this library has issued in this process (a
  * CUDA-graph launch counts each kernel node it runs). */

@@ -68,6 +68,9 @@ _SIGNATURES = {
     "usp_batch_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
                                   _P(c_double), _P(Result), _P(c_int32)]),
     "usp_batch_history": (c_int32, [c_void_p, c_int32, _P(c_double), c_int32, _P(c_int32)]),
+    "usp_solve_many": (c_int32, [_P(c_void_p), c_int32, _P(c_void_p), _P(c_void_p), c_int32,
+                                 c_double, c_int32, _P(Result), _P(c_int32)]),
+    "usp_autotune": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, _P(Options)]),
     "usp_solver_set_options": (c_int32, [c_void_p, _P(Options)]),
     "usp_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
                             c_double, _P(Result)]),

@@ -178,6 +178,107 @@ __device__ __forceinline__ void out_to_in(const V* o, V* i) {
     for (int k2 = 0; k2 < N2; ++k2) i[s + S * k2] = o[s * N2 + k2];
 }
 
+// ---- lines of length N = R * M (R in {1, 2, 3}, M = 2^k <= 256) -----------
+//
+// A length-N transform with N = R M splits by decimation in time into R
+// interleaved sub-sequences x[R m + r] (m < M), each transformed by the
+// M-point code above:  X[k + M j] = sum_r W_3^(r j) (W_N^(r k) Y_r[k]),
+// Y_r = DFT_M(x[R . + r]) (W_R for R = 2: +-1).  A line uses G = R * G_M
+// threads; thread l = r G_M + g runs sub-sequence r with the M-point layout of
+// thread g and, after one exchange through shared memory, holds the outputs
+// X[k + M r] for the frequencies k of thread g.  The inverse runs the same
+// steps backwards.  Positions of register q of line thread l (r = l / G_M,
+// g = l % G_M):
+//   spatial input  (stage-1 order)   R in_index<M>(g, q)  + r
+//   spatial output (after inverse)   R out_index<M>(g, q) + r
+//   spectral output (after forward)  out_index<M>(g, q) + M r
+//   spectral input (for an inverse)  in_index<M>(g, q)  + M r
+// For R = 1 these are the plain M-point positions.
+template <int N>
+struct Line {
+  static constexpr int R = (N % 3 == 0) ? 3 : (N > 256 ? 2 : 1);
+  static constexpr int M = N / R;
+  static constexpr int GM = Split<M>::G;
+  static constexpr int G = R * GM;        // threads per line
+  static constexpr int NV = Split<M>::N1;  // values per thread
+  static_assert(R * M == N && (M & (M - 1)) == 0 && M <= 256, "unsupported line length");
+  static __device__ __forceinline__ int sp_in(int l, int q) { return R * in_index<M>(l % GM, q) + l / GM; }
+  static __device__ __forceinline__ int sp_out(int l, int q) { return R * out_index<M>(l % GM, q) + l / GM; }
+  static __device__ __forceinline__ int fr_out(int l, int q) { return out_index<M>(l % GM, q) + M * (l / GM); }
+  static __device__ __forceinline__ int fr_in(int l, int q) { return in_index<M>(l % GM, q) + M * (l / GM); }
+};
+
+// sqrt(3)/2: the imaginary part of exp(2 pi i / 3).
+#define USP_SQRT3_HALF 0.86602540378443864676
+
+// Output j of the radix-R butterfly over a[0..R) (forward: W_3 = exp(-2 pi i/3)).
+template <int R, bool INV, typename V>
+__device__ __forceinline__ V radix_out(const V* a, int j) {
+  typedef decltype(a[0].x) T;
+  if (R == 2) return j == 0 ? cadd(a[0], a[1]) : csub(a[0], a[1]);
+  const V s = cadd(a[1], a[2]), d = csub(a[1], a[2]);
+  if (j == 0) return cadd(a[0], s);
+  const V t = mkc<V>(a[0].x - T(0.5) * s.x, a[0].y - T(0.5) * s.y);
+  const V u = mkc<V>(T(USP_SQRT3_HALF) * d.x, T(USP_SQRT3_HALF) * d.y);
+  // forward: X1 = t - i u, X2 = t + i u; the inverse swaps the signs
+  const bool minus_i = (j == 1) != INV;
+  return minus_i ? mkc<V>(t.x + u.y, t.y - u.x) : mkc<V>(t.x - u.y, t.y + u.x);
+}
+
+// The radix-R stage after the M-point forward transforms.  v: this
+// thread's outputs Y_r[k], k = out_index<M>(g, q); ex: the line's exchange
+// area, element e at ex[e * STRIDE + lane]; rtw[m] = W_N^m.  On return
+// v[q] = X[out_index<M>(g, q) + M r].  Begins and ends with a barrier-free
+// hand-off: the caller's transform already synchronised after its own use of
+// ex, and this function synchronises after its reads.
+template <int N, int STRIDE, typename V>
+__device__ __forceinline__ void radix_fwd(V* v, V* ex, const V* rtw, int l, int lane) {
+  typedef Line<N> L;
+  if (L::R == 1) return;
+  constexpr int M = L::M, NV = L::NV;
+  const int r = l / L::GM, g = l % L::GM;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int k = out_index<M>(g, q);
+    const V w = v[q];
+    ex[(r * M + k) * STRIDE + lane] = r == 0 ? w : cmul(w, rtw[r * k]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int k = out_index<M>(g, q);
+    V a[L::R];
+#pragma unroll
+    for (int i = 0; i < L::R; ++i) a[i] = ex[(i * M + k) * STRIDE + lane];
+    v[q] = radix_out<L::R, false>(a, r);
+  }
+  __syncthreads();
+}
+
+// The radix-R stage before the M-point inverse transforms: v[q] =
+// X[in_index<M>(g, q) + M r] in; Z_r[k] = W_N^(-r k) sum_j W_R^(-r j)
+// X[k + M j] out (k = in_index<M>(g, q)), ready for the M-point inverse.
+template <int N, int STRIDE, typename V>
+__device__ __forceinline__ void radix_inv(V* v, V* ex, const V* rtw, int l, int lane) {
+  typedef Line<N> L;
+  if (L::R == 1) return;
+  constexpr int M = L::M, NV = L::NV;
+  const int r = l / L::GM, g = l % L::GM;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) ex[(r * M + in_index<M>(g, q)) * STRIDE + lane] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int k = in_index<M>(g, q);
+    V a[L::R];
+#pragma unroll
+    for (int i = 0; i < L::R; ++i) a[i] = ex[(i * M + k) * STRIDE + lane];
+    const V z = radix_out<L::R, true>(a, r);
+    v[q] = r == 0 ? z : cmulc(z, rtw[r * k]);
+  }
+  __syncthreads();
+}
+
 // Frequency index k in [0,n) to signed FFT-order m in [-n/2, n/2).
 __device__ __forceinline__ int signed_freq(int k, int n) { return k < (n >> 1) ? k : k - n; }
 

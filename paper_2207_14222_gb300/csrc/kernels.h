@@ -207,6 +207,7 @@ cudaError_t launch_cols_f32(int n, const ColsArgs<float>& a, cudaStream_t s);
 cudaError_t launch_cols_f64(int n, const ColsArgs<double>& a, cudaStream_t s);
 int rows_per_block_f32(int n);
 int rows_per_block_f64(int n);
+int cols_per_block(int n);   // columns per block of the plain strided-axis pass
 
 // Auxiliary kernels (pencil_kernels.cu).
 cudaError_t init_twiddles();

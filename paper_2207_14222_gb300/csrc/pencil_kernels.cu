@@ -38,6 +38,19 @@ __device__ __forceinline__ float2 tw_entry<float>(int m) { return g_tw32[m]; }
 template <>
 __device__ __forceinline__ double2 tw_entry<double>(int m) { return g_tw64[m]; }
 
+// W_1536^m, m in [0,1536): the radix stage of lines of length 96, 192, 384
+// (W_N^m = W_1536^(m 1536/N)) and 512.
+constexpr int TWX_LEN = 1536;
+__device__ float2 g_twx32[TWX_LEN];
+__device__ double2 g_twx64[TWX_LEN];
+
+template <typename T>
+__device__ __forceinline__ typename cplx_of<T>::type twx_entry(int m);
+template <>
+__device__ __forceinline__ float2 twx_entry<float>(int m) { return g_twx32[m]; }
+template <>
+__device__ __forceinline__ double2 twx_entry<double>(int m) { return g_twx64[m]; }
+
 // FP32 rows: 4 blocks of 256 threads per SM (64 registers) -- measured
 // 3.77 TB/s for the fused rows pass versus 3.45 TB/s at 3 blocks (80
 // registers) and 1.88 TB/s when ptxas is left to use 210 registers.
@@ -49,6 +62,22 @@ template <> struct RowsCfg<float> {
 template <> struct RowsCfg<double> {
   static constexpr int THREADS = 128;
   static constexpr int MINB = 1;
+};
+// Block shape of the line pass for lines of length N: radix-3 lines use
+// 3/4 of the threads so that whole lines fill a block.
+template <typename T, int N>
+struct RowsShape {
+  static constexpr int THREADS = Line<N>::R == 3 ? RowsCfg<T>::THREADS * 3 / 4 : RowsCfg<T>::THREADS;
+  static constexpr int F = THREADS / Line<N>::G;  // lines per block
+  // the radix stage of the longest lines needs more than 64 registers
+  static constexpr int MINB = N >= 384 && RowsCfg<T>::MINB > 2 ? 2 : RowsCfg<T>::MINB;
+  static_assert(F * Line<N>::G == THREADS, "lines must fill the block");
+};
+// Columns per block of the strided-axis pass (lanes per line thread).
+template <int N>
+struct ColsShape {
+  static constexpr int COLS = N >= 384 ? 16 : 32;
+  static constexpr int THREADS = COLS * Line<N>::G;
 };
 
 // ------------------------------------------------------------ reductions ---
@@ -145,20 +174,38 @@ __device__ __forceinline__ void fft_rows(V* v, V* exr, const V* tw, int g) {
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
+// Line transforms (rows): forward from the stage-1 spatial order to the
+// spectral output order, inverse from the spectral input order to the
+// spatial output order (Line<N>).  exr: the line's N-element exchange area.
+template <int N, typename V>
+__device__ __forceinline__ void line_fwd_rows(V* v, V* exr, const V* tw, const V* rtw, int l) {
+  typedef Line<N> L;
+  fft_rows<L::M, false>(v, exr + (l / L::GM) * L::M, tw, l % L::GM);
+  radix_fwd<N, 1>(v, exr, rtw, l, 0);
+}
+template <int N, typename V>
+__device__ __forceinline__ void line_inv_rows(V* v, V* exr, const V* tw, const V* rtw, int l) {
+  typedef Line<N> L;
+  radix_inv<N, 1>(v, exr, rtw, l, 0);
+  fft_rows<L::M, true>(v, exr + (l / L::GM) * L::M, tw, l % L::GM);
+}
+
 __device__ __forceinline__ float2 load_v(const void* V, int64_t i, bool vreal) {
   if (vreal) return make_float2(__ldg(reinterpret_cast<const float*>(V) + i), 0.f);
   return __ldg(reinterpret_cast<const float2*>(V) + i);
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(const RowsArgs<T> a) {
+__global__ void __launch_bounds__(RowsShape<T, N>::THREADS, RowsShape<T, N>::MINB) k_rows(const RowsArgs<T> a) {
   typedef typename cplx_of<T>::type V;
-  constexpr int N1 = Split<N>::N1, G = Split<N>::G;
-  constexpr int THREADS = RowsCfg<T>::THREADS;
-  constexpr int F = THREADS / G;  // rows per block
+  typedef Line<N> L;
+  constexpr int N1 = L::NV, G = L::G, M = L::M;
+  constexpr int THREADS = RowsShape<T, N>::THREADS;
+  constexpr int F = RowsShape<T, N>::F;  // rows per block
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw = reinterpret_cast<V*>(smem_raw);
-  V* ex = tw + N;
+  V* tw = reinterpret_cast<V*>(smem_raw);   // M-point stage-1 twiddles
+  V* rtw = tw + M;                          // W_N^m (radix stage), R > 1
+  V* ex = rtw + (L::R > 1 ? N : 0);
 
   // the problem of this block (blocks never straddle problems)
   const int p = a.bt.count > 1 ? int((int64_t)blockIdx.x * F / a.bt.rows_per) : 0;
@@ -171,15 +218,19 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
   const int64_t base = row * N;
   const bool xzero = (a.flags & F_XZERO) != 0;
   const bool vreal = (a.flags & F_VREAL) != 0;
-  for (int m = tid; m < N; m += THREADS) tw[m] = tw_entry<T>(stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N));
+  for (int m = tid; m < M; m += THREADS) tw[m] = tw_entry<T>(stage1_twiddle_exponent(m, Split<M>::N2) * (256 / M));
+  if (L::R > 1)
+    for (int m = tid; m < N; m += THREADS) rtw[m] = twx_entry<T>(m * (TWX_LEN / N));
   __syncthreads();
   V* exr = ex + f * N;
+  // spectral input (an inverse transform without a forward one) or spatial
+  const bool in_spec = (a.mode & R_IN_BUF) && !(a.mode & R_FWD);
 
   V v[N1];
-  // ---- input stage (stage-1 distribution: register q holds index N2 q + g)
+  // ---- input stage (register q holds position L::sp_in / L::fr_in)
 #pragma unroll
   for (int q = 0; q < N1; ++q) {
-    const int64_t i = base + in_index<N>(g, q);
+    const int64_t i = base + (in_spec ? L::fr_in(g, q) : L::sp_in(g, q));
     V t = mkc<V>(T(0), T(0));
     if (active) {
       if (a.mode & R_IN_BUF) {
@@ -203,30 +254,32 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
     v[q] = t;
   }
   // ---- transforms
-  if (a.mode & R_FWD) fft_rows<N, false>(v, exr, tw, g);
+  if (a.mode & R_FWD) line_fwd_rows<N>(v, exr, tw, rtw, g);
   if (a.mode & R_MUL) {
     const Sym<T> sy = problem_sym(a.sym, a.bt, p);
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
-      const int k = out_index<N>(g, q);
+      const int k = L::fr_out(g, q);
       v[q] = cmul(v[q], spectral_factor<T, V>(axis_p2(sy, 0, k), sy, a.mul));
     }
   }
   if (a.mode & R_INV) {
     if (a.mode & R_FWD) {
       V t[N1];
-      out_to_in<N>(v, t);
+      out_to_in<M>(v, t);
 #pragma unroll
       for (int q = 0; q < N1; ++q) v[q] = t[q];
     }
-    fft_rows<N, true>(v, exr, tw, g);
+    line_inv_rows<N>(v, exr, tw, rtw, g);
   }
-  // ---- output stage (register q holds index out_index(g, q))
+  // ---- output stage (register q holds position L::sp_out after an
+  // inverse, L::fr_out after a forward transform alone)
   if (a.mode & R_OUT_BUF) {
     if (active) {
+      const bool spec = !(a.mode & R_INV);
 #pragma unroll
       for (int q = 0; q < N1; ++q)
-        reinterpret_cast<V*>(a.buf)[base + out_index<N>(g, q)] = v[q];
+        reinterpret_cast<V*>(a.buf)[base + (spec ? L::fr_out(g, q) : L::sp_out(g, q))] = v[q];
     }
     return;
   }
@@ -238,7 +291,7 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
       const float al = a.bt.alpha ? a.bt.alpha[p] : float(a.alpha);
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
-        const int64_t i = base + out_index<N>(g, q);
+        const int64_t i = base + L::sp_out(g, q);
         const float2 vv = load_v(a.V, i, vreal);
         const float2 xv = xzero ? make_float2(0.f, 0.f) : a.x_in[i];
         const float ur = float(v[q].x) - xv.x, ui = float(v[q].y) - xv.y;
@@ -256,14 +309,14 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
     }
     if (then_pre) {
       V t[N1];
-      out_to_in<N>(v, t);
+      out_to_in<M>(v, t);
 #pragma unroll
       for (int q = 0; q < N1; ++q) v[q] = t[q];
-      fft_rows<N, false>(v, exr, tw, g);
+      line_fwd_rows<N>(v, exr, tw, rtw, g);
       if (active) {
 #pragma unroll
         for (int q = 0; q < N1; ++q)
-          reinterpret_cast<V*>(a.buf)[base + out_index<N>(g, q)] = v[q];
+          reinterpret_cast<V*>(a.buf)[base + L::fr_out(g, q)] = v[q];
       }
     }
     const int64_t bpp = a.bt.count > 1 ? a.bt.rows_per / F : (int64_t)gridDim.x;
@@ -277,7 +330,7 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
     if (active) {
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
-        const int64_t i = base + out_index<N>(g, q);
+        const int64_t i = base + L::sp_out(g, q);
         const float2 vv = load_v(a.V, i, vreal);
         const float2 xv = a.x_in[i];
         const double ax = double(v[q].x) + (double(vv.x) * xv.x - double(vv.y) * xv.y);
@@ -305,19 +358,19 @@ __global__ void __launch_bounds__(RowsCfg<T>::THREADS, RowsCfg<T>::MINB) k_rows(
 
 // ------------------------------------------------------------ columns ---
 
-template <int N, bool INV, typename V>
+template <int N, bool INV, int COLS, typename V>
 __device__ __forceinline__ void fft_cols(V* v, V* ex, const V* tw, int g, int lane) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
   stage1<N, INV>(v, g, tw);
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * 32 + lane] = v[k1];
+  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * COLS + lane] = v[k1];
   __syncthreads();
   V w[N1];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int k1 = g + G * s;
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * 32 + lane];
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * COLS + lane];
   }
   __syncthreads();
   stage2<N, INV>(w);
@@ -325,35 +378,60 @@ __device__ __forceinline__ void fft_cols(V* v, V* ex, const V* tw, int g, int la
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
+// Line transforms along a strided axis (COLS columns per block, lane =
+// column); orders as line_fwd_rows / line_inv_rows.
+template <int N, int COLS, typename V>
+__device__ __forceinline__ void line_fwd_cols(V* v, V* ex, const V* tw, const V* rtw, int l, int lane) {
+  typedef Line<N> L;
+  fft_cols<L::M, false, COLS>(v, ex + (l / L::GM) * L::M * COLS, tw, l % L::GM, lane);
+  radix_fwd<N, COLS>(v, ex, rtw, l, lane);
+}
+template <int N, int COLS, typename V>
+__device__ __forceinline__ void line_inv_cols(V* v, V* ex, const V* tw, const V* rtw, int l, int lane) {
+  typedef Line<N> L;
+  radix_inv<N, COLS>(v, ex, rtw, l, lane);
+  fft_cols<L::M, true, COLS>(v, ex + (l / L::GM) * L::M * COLS, tw, l % L::GM, lane);
+}
+
 template <typename T, int N>
-__global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) {
+__global__ void __launch_bounds__(ColsShape<N>::THREADS) k_cols(const ColsArgs<T> a) {
   typedef typename cplx_of<T>::type V;
-  constexpr int N1 = Split<N>::N1;
+  typedef Line<N> L;
+  constexpr int N1 = L::NV, M = L::M, COLS = ColsShape<N>::COLS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw = reinterpret_cast<V*>(smem_raw);
-  V* ex = tw + N;
+  V* tw = reinterpret_cast<V*>(smem_raw);   // M-point stage-1 twiddles
+  V* rtw = tw + M;                          // W_N^m (radix stage), R > 1
+  V* ex = rtw + (L::R > 1 ? N : 0);
 
   const int64_t ib = blockIdx.x % a.inner_blocks, o = blockIdx.x / a.inner_blocks;
   const int p = a.bt.count > 1 ? int(o / a.bt.outer_per) : 0;
   if (!(a.flags & F_NOSTATE) && a.st[p].done) return;
 
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int64_t col = ib * 32 + lane;
+  const int lane = threadIdx.x % COLS, g = threadIdx.x / COLS;
+  const int64_t col = ib * COLS + lane;
   const bool active = col < a.inner;
   const int64_t base = o * (int64_t)N * a.inner + col;
   V* buf = reinterpret_cast<V*>(a.buf);
-  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = tw_entry<T>(stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N));
+  for (int m = threadIdx.x; m < M; m += blockDim.x)
+    tw[m] = tw_entry<T>(stage1_twiddle_exponent(m, Split<M>::N2) * (256 / M));
+  if (L::R > 1)
+    for (int m = threadIdx.x; m < N; m += blockDim.x) rtw[m] = twx_entry<T>(m * (TWX_LEN / N));
   __syncthreads();
 
+  // COL_INV reads a spectrum along this axis, the other modes spatial values
+  const bool in_spec = a.mode == COL_INV;
   V v[N1];
 #pragma unroll
   for (int q = 0; q < N1; ++q)
-    v[q] = active ? buf[base + (int64_t)in_index<N>(g, q) * a.inner] : mkc<V>(T(0), T(0));
+    v[q] = active ? buf[base + (int64_t)(in_spec ? L::fr_in(g, q) : L::sp_in(g, q)) * a.inner]
+                  : mkc<V>(T(0), T(0));
 
+  bool out_spec = false;
   if (a.mode == COL_INV) {
-    fft_cols<N, true>(v, ex, tw, g, lane);
+    line_inv_cols<N, COLS>(v, ex, tw, rtw, g, lane);
   } else {
-    fft_cols<N, false>(v, ex, tw, g, lane);
+    line_fwd_cols<N, COLS>(v, ex, tw, rtw, g, lane);
+    out_spec = true;
     if (a.mode == COL_FWD_MUL_INV) {
       // This pass runs on axis 0 after all faster axes were transformed, so
       // the column index decomposes into their frequency indices.
@@ -371,18 +449,20 @@ __global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) 
       V t[N1];
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
-        const int k = out_index<N>(g, q);
+        const int k = L::fr_out(g, q);
         v[q] = cmul(v[q], spectral_factor<T, V>(p2in + axis_p2(sy, 0, k), sy, a.mul));
       }
-      out_to_in<N>(v, t);
+      out_to_in<M>(v, t);
 #pragma unroll
       for (int q = 0; q < N1; ++q) v[q] = t[q];
-      fft_cols<N, true>(v, ex, tw, g, lane);
+      line_inv_cols<N, COLS>(v, ex, tw, rtw, g, lane);
+      out_spec = false;
     }
   }
   if (active) {
 #pragma unroll
-    for (int q = 0; q < N1; ++q) buf[base + (int64_t)out_index<N>(g, q) * a.inner] = v[q];
+    for (int q = 0; q < N1; ++q)
+      buf[base + (int64_t)(out_spec ? L::fr_out(g, q) : L::sp_out(g, q)) * a.inner] = v[q];
   }
 }
 
@@ -391,12 +471,12 @@ __global__ void __launch_bounds__(32 * Split<N>::G) k_cols(const ColsArgs<T> a) 
 template <typename T, int N>
 static size_t rows_smem() {
   typedef typename cplx_of<T>::type V;
-  return sizeof(V) * (N + (RowsCfg<T>::THREADS / Split<N>::G) * N);
+  return sizeof(V) * (Line<N>::M + (Line<N>::R > 1 ? N : 0) + RowsShape<T, N>::F * N);
 }
 template <typename T, int N>
 static size_t cols_smem() {
   typedef typename cplx_of<T>::type V;
-  return sizeof(V) * (N + 32 * N);
+  return sizeof(V) * (Line<N>::M + (Line<N>::R > 1 ? N : 0) + ColsShape<N>::COLS * N);
 }
 
 template <typename T, int N>
@@ -412,13 +492,13 @@ static cudaError_t cols_attr() {
 
 template <typename T, int N>
 static cudaError_t rows_go(const RowsArgs<T>& a, int64_t grid, cudaStream_t s) {
-  k_rows<T, N><<<(unsigned)grid, RowsCfg<T>::THREADS, rows_smem<T, N>(), s>>>(a);
+  k_rows<T, N><<<(unsigned)grid, RowsShape<T, N>::THREADS, rows_smem<T, N>(), s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int N>
 static cudaError_t cols_go(const ColsArgs<T>& a, cudaStream_t s) {
   const int64_t grid = a.inner_blocks * a.outer;
-  k_cols<T, N><<<(unsigned)grid, 32 * Split<N>::G, cols_smem<T, N>(), s>>>(a);
+  k_cols<T, N><<<(unsigned)grid, ColsShape<N>::THREADS, cols_smem<T, N>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -432,6 +512,10 @@ static cudaError_t cols_go(const ColsArgs<T>& a, cudaStream_t s) {
     case 64: return CALL(64);                     \
     case 128: return CALL(128);                   \
     case 256: return CALL(256);                   \
+    case 96: return CALL(96);                     \
+    case 192: return CALL(192);                   \
+    case 384: return CALL(384);                   \
+    case 512: return CALL(512);                   \
     default: return cudaErrorInvalidValue;        \
   }
 
@@ -456,8 +540,24 @@ cudaError_t launch_cols_f64(int n, const ColsArgs<double>& a, cudaStream_t s) {
 #undef C_
 }
 
-int rows_per_block_f32(int n) { return RowsCfg<float>::THREADS / (n / (1 << ((ilog2c(n) + 1) / 2))); }
-int rows_per_block_f64(int n) { return RowsCfg<double>::THREADS / (n / (1 << ((ilog2c(n) + 1) / 2))); }
+static int switch_rows_f32(int n) {
+#define C_(N) RowsShape<float, N>::F
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+static int switch_rows_f64(int n) {
+#define C_(N) RowsShape<double, N>::F
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+static int switch_cols(int n) {
+#define C_(N) ColsShape<N>::COLS
+  USP_SWITCH_N(n, C_)
+#undef C_
+}
+int rows_per_block_f32(int n) { return switch_rows_f32(n); }
+int rows_per_block_f64(int n) { return switch_rows_f64(n); }
+int cols_per_block(int n) { return switch_cols(n); }
 
 template <typename T, int N>
 static cudaError_t attrs_one() {
@@ -475,7 +575,11 @@ static cudaError_t attrs_all() {
   if ((e = attrs_one<T, 32>()) != cudaSuccess) return e;
   if ((e = attrs_one<T, 64>()) != cudaSuccess) return e;
   if ((e = attrs_one<T, 128>()) != cudaSuccess) return e;
-  return attrs_one<T, 256>();
+  if ((e = attrs_one<T, 256>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 96>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 192>()) != cudaSuccess) return e;
+  if ((e = attrs_one<T, 384>()) != cudaSuccess) return e;
+  return attrs_one<T, 512>();
 }
 
 // Twiddles from the first octant by symmetry, so W^(64 j) are exactly
@@ -486,33 +590,45 @@ const float2* twiddle_table_f32() {
   return static_cast<const float2*>(p);
 }
 
-cudaError_t init_twiddles() {
-  float2 h32[256];
-  double2 h64[256];
+// exp(-2 pi i m / L) for m in [0, L), L a multiple of 8, from the first
+// octant by symmetry (quarter turns are exact).
+static void unit_roots(int L, double2* out) {
   const double two_pi = 6.283185307179586476925286766559;
-  for (int m = 0; m < 256; ++m) {
-    const int q = m / 64, r = m % 64;
-    double c, s;  // cos, sin of 2 pi r/256, r in [0, 64)
-    if (r <= 32) {
-      c = cos(two_pi * r / 256.0);
-      s = sin(two_pi * r / 256.0);
+  const int Q = L / 4;
+  for (int m = 0; m < L; ++m) {
+    const int q = m / Q, r = m % Q;
+    double c, s;  // cos, sin of 2 pi r/L, r in [0, L/4)
+    if (2 * r <= Q) {
+      c = cos(two_pi * r / L);
+      s = sin(two_pi * r / L);
     } else {
-      c = sin(two_pi * (64 - r) / 256.0);
-      s = cos(two_pi * (64 - r) / 256.0);
+      c = sin(two_pi * (Q - r) / L);
+      s = cos(two_pi * (Q - r) / L);
     }
     if (r == 0) { c = 1.0; s = 0.0; }
-    // rotate by q quarter turns: angle 2 pi m/256 = q pi/2 + 2 pi r/256
-    for (int k = 0; k < q; ++k) {
+    for (int k = 0; k < q; ++k) {  // rotate by q quarter turns
       const double t = c;
       c = -s;
       s = t;
     }
-    h64[m] = make_double2(c, -s);  // exp(-i angle)
-    h32[m] = make_float2((float)c, (float)-s);
+    out[m] = make_double2(c, -s);
   }
+}
+
+cudaError_t init_twiddles() {
+  static double2 h64[256], x64[TWX_LEN];
+  static float2 h32[256], x32[TWX_LEN];
+  unit_roots(256, h64);
+  unit_roots(TWX_LEN, x64);
+  for (int m = 0; m < 256; ++m) h32[m] = make_float2((float)h64[m].x, (float)h64[m].y);
+  for (int m = 0; m < TWX_LEN; ++m) x32[m] = make_float2((float)x64[m].x, (float)x64[m].y);
   cudaError_t e = cudaMemcpyToSymbol(g_tw32, h32, sizeof(h32));
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(g_tw64, h64, sizeof(h64));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(g_twx32, x32, sizeof(x32));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(g_twx64, x64, sizeof(x64));
   if (e != cudaSuccess) return e;
   if ((e = attrs_all<float>()) != cudaSuccess) return e;
   return attrs_all<double>();

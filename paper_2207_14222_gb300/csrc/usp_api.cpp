@@ -17,9 +17,12 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <tuple>
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.h"
@@ -136,6 +139,9 @@ struct usp_solver {
 };
 
 static bool is_pow2_in_range(int64_t v) { return v >= 2 && v <= 256 && (v & (v - 1)) == 0; }
+// Axis lengths the line kernels transform: 2^k in [2, 256], and 3 * 2^k or
+// 2 * 256 through their radix-3 / radix-2 outer stage.
+static bool supported_length(int64_t v) { return is_pow2_in_range(v) || v == 96 || v == 192 || v == 384 || v == 512; }
 
 static void free_graphs(usp_solver* s) {
   for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
@@ -178,6 +184,7 @@ static void build_maps(usp_solver* s) {
   if (s->ndim < 2) return;
   bool ok = true;
   for (int axis = 0; axis < s->ndim - 1 && axis < 2; ++axis) {
+    if (!is_pow2_in_range(s->n[axis])) return;  // the staged kernels take 2^k <= 256
     int64_t inner = 1, outer = 1;
     for (int ax = axis + 1; ax < s->ndim; ++ax) inner *= s->n[ax];
     for (int ax = 0; ax < axis; ++ax) outer *= s->n[ax];
@@ -230,7 +237,8 @@ static ColsArgs<T> cols_args(const usp_solver* s, int axis, int mode, int mul, i
   outer *= s->B;  // problems are stacked along a new slowest axis
   c.inner = inner;
   c.outer = outer;
-  c.inner_blocks = (inner + 31) / 32;
+  const int cols = cols_per_block(s->n[axis]);
+  c.inner_blocks = (inner + cols - 1) / cols;
   c.buf = buf;
   c.st = s->st;
   c.sym = sym;
@@ -561,8 +569,9 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   int64_t N = 1;
   for (int ax = 0; ax < grid->ndim; ++ax) {
     if (grid->n[ax] < 1) return fail(USP_ERR_INVALID_ARG, "axis %d has length %lld", ax, (long long)grid->n[ax]);
-    if (!is_pow2_in_range(grid->n[ax]))
-      return fail(USP_ERR_UNSUPPORTED_SIZE, "axis %d length %lld is not a power of two in [2, 256]",
+    if (!supported_length(grid->n[ax]))
+      return fail(USP_ERR_UNSUPPORTED_SIZE,
+                  "axis %d length %lld is not supported (powers of two in [2, 256], 96, 192, 384, 512)",
                   ax, (long long)grid->n[ax]);
     N *= grid->n[ax];
   }
@@ -1051,6 +1060,56 @@ extern "C" usp_status usp_batch_solve(usp_solver* s, const void* y, void* x, int
   return st;
 }
 
+extern "C" usp_status usp_solve_many(usp_solver* const* solvers, int32_t count,
+                                     const void* const* ys, void* const* xs, int32_t use_x0,
+                                     double tol, int32_t maxit, usp_result* results,
+                                     usp_status* statuses) {
+  if (count < 1 || !solvers || !ys || !xs) return fail(USP_ERR_INVALID_ARG, "bad argument");
+  std::vector<int64_t> first(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (solvers[j] == solvers[i]) return fail(USP_ERR_INVALID_ARG, "solver %d is listed twice", i);
+    usp_status st = check_solve_args(solvers[i], ys[i], xs[i], tol, maxit);
+    if (st != USP_OK) return st;
+    first[i + 1] = first[i] + solvers[i]->B;
+  }
+  // one host thread per solver: each drives its own stream and graphs, so
+  // the solvers' passes run concurrently on the GPU
+  std::vector<usp_status> st(count, USP_OK);
+  std::vector<std::string> msg(count);
+  auto run = [&](int i) {
+    usp_solver* s = solvers[i];
+    usp_result* r = results ? results + first[i] : nullptr;
+    usp_status* ps = statuses ? statuses + first[i] : nullptr;
+    if (cudaSetDevice(s->device) != cudaSuccess) {
+      st[i] = fail(USP_ERR_CUDA, "cudaSetDevice(%d) failed", s->device);
+    } else {
+      cudaError_t e = cudaEventRecord(s->ev, s->user_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev, 0);
+      st[i] = e == cudaSuccess
+                  ? solve_impl(s, (const float2*)ys[i], (float2*)xs[i], use_x0, tol, maxit,
+                               nullptr, r, ps)
+                  : fail(USP_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
+      cudaStreamSynchronize(s->stream);
+    }
+    msg[i] = g_last_error;
+  };
+  int cur = 0;
+  cudaGetDevice(&cur);
+  std::vector<std::thread> threads;
+  threads.reserve(count);
+  for (int i = 1; i < count; ++i) threads.emplace_back(run, i);
+  run(0);
+  for (auto& t : threads) t.join();
+  cudaSetDevice(cur);
+  for (int i = 0; i < count; ++i)
+    if (st[i] != USP_OK) {
+      g_last_error = msg[i];
+      return st[i];
+    }
+  return USP_OK;
+}
+
 extern "C" usp_status usp_batch_history(const usp_solver* s, int32_t problem, double* host_out,
                                         int32_t capacity, int32_t* n_out) {
   if (!s || !n_out) return fail(USP_ERR_INVALID_ARG, "NULL argument");
@@ -1225,4 +1284,71 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
   }
   if (cur != s->device) cudaSetDevice(cur);
   return res;
+}
+
+// ------------------------------------------------------------ autotune ---
+
+// Chosen options per (ndim, n0, n1, n2, problems, real V): the first solver of
+// a shape is timed, later ones reuse the choice.
+typedef std::tuple<int, int, int, int, int, int> TuneKey;
+static std::map<TuneKey, usp_options> g_tuned;
+static std::mutex g_tuned_mu;
+
+extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_t iters,
+                                   usp_options* chosen) {
+  if (!s || !y || !x || iters < 1) return fail(USP_ERR_INVALID_ARG, "bad argument");
+  const TuneKey key{s->ndim, s->n[0], s->n[1], s->n[2], s->B, s->vreal ? 1 : 0};
+  usp_options best = s->opt;
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      best = it->second;
+      best.plain = s->opt.plain;
+      best.max_refinements = s->opt.max_refinements;
+      usp_status st = usp_solver_set_options(s, &best);
+      if (st == USP_OK && chosen) *chosen = best;
+      return st;
+    }
+  }
+  // candidates: pass schedule x staged (TMA) or plain loads
+  std::vector<usp_options> cands;
+  const int nx = s->n[s->ndim - 1];
+  const bool staged = s->maps_ok || nx == 128 || nx == 256;
+  for (int sched = 1; sched <= (fused_supported(s) ? 2 : 1); ++sched)
+    for (int nt = 0; nt <= (staged ? 1 : 0); ++nt) {
+      usp_options o = s->opt;
+      o.schedule = sched;
+      o.no_tma = nt;
+      cands.push_back(o);
+    }
+  const usp_options keep = s->opt;
+  double best_ms = 1e300;
+  for (const usp_options& o : cands) {
+    usp_status st = usp_solver_set_options(s, &o);
+    if (st != USP_OK) return st;
+    usp_pass_time pt[16];
+    int32_t np = 0;
+    st = usp_time_passes(s, y, x, iters, pt, 16, &np);
+    if (st != USP_OK) {
+      usp_solver_set_options(s, &keep);
+      return st;
+    }
+    double ms = 0.0;
+    for (int k = 0; k < np && k < 16; ++k) ms += pt[k].ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = o;
+    }
+  }
+  // iterations per graph launch: about 0.2 ms of GPU work between polls
+  best.chunk = (int)std::min(64.0, std::max(4.0, std::round(0.2 / std::max(best_ms, 1e-6))));
+  usp_status st = usp_solver_set_options(s, &best);
+  if (st != USP_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned[key] = best;
+  }
+  if (chosen) *chosen = best;
+  return USP_OK;
 }

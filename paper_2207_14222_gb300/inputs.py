@@ -184,3 +184,29 @@ def random_field(shape, seed, complex_=True):
     if complex_:
         return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     return rng.standard_normal(shape)
+
+
+BATCH_SIDES = (64, 96, 128, 192, 256, 384, 512)
+
+
+def batch_problem(i, seed0=1000):
+    """Problem ``i`` of the mixed-size batch of 2-D problems: seed seed0 + i;
+    side drawn uniformly from BATCH_SIDES; smoothing sigma uniform in
+    [2, 8] px; even i: Helmholtz with n in [1, 1.5] (the smoothed field
+    rescaled to that range), absorbing layer side/8 px, centre point source;
+    odd i: steady diffusion with log-normal absorption (median 0.01/px,
+    sigma_log 0.5, D = 1), centre point source."""
+    rng = np.random.default_rng(seed0 + i)
+    side = int(BATCH_SIDES[rng.integers(len(BATCH_SIDES))])
+    sigma = float(rng.uniform(2.0, 8.0))
+    shape = (side, side)
+    g = smooth_field(shape, sigma, rng)
+    S = _centre_point_source(shape, 1.0)
+    if i % 2 == 0:
+        g = (g - g.min()) / (g.max() - g.min())
+        k2 = helmholtz_medium(shape, 1.0 + 0.5 * g, side // 8)
+        return dict(kind="helmholtz", k2=k2, S=S, dx=1.0, k0=K0_QUARTER_WAVE,
+                    seed=seed0 + i, sigma_px=sigma)
+    eta = 0.01 * np.exp(0.5 * g)
+    return dict(kind="diffusion", eta=eta, D=1.0, S=S, dx=1.0, seed=seed0 + i,
+                sigma_px=sigma)

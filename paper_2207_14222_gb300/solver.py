@@ -26,8 +26,8 @@ class Solver:
     """Fixed-point iteration with the universal split preconditioner for the
     canonical system (L + V) x = y (Algorithm 1, forward-eliminated form).
 
-    shape : grid shape (1-3 axes, each a power of two in [2, 256]), last axis
-            fastest.
+    shape : grid shape (1-3 axes, each a power of two in [2, 256] or 96, 192,
+            384, 512), last axis fastest.
     a, b  : symbol Lhat(p) = a |p|^2 + b (complex).
     V     : CUDA tensor of the potential, complex64 (or float32 for a real
             potential), copied at construction.
@@ -130,6 +130,20 @@ class Solver:
                                              ctypes.byref(n)))
         return [dict(name=out[i].name.decode(), ms=out[i].ms, bytes=out[i].bytes,
                      launches=out[i].launches) for i in range(n.value)]
+
+    def autotune(self, y, x=None, iters=5):
+        """Time the pass variants this grid admits on (y, x) and keep the
+        fastest (cached per grid shape for the process); returns the chosen
+        options as a dict.  x, if given, is overwritten."""
+        import torch
+        y = y.contiguous()
+        if x is None:
+            x = torch.empty_like(y)
+        o = Options()
+        with torch.cuda.device(self.device):
+            check(_lib.lib().usp_autotune(self._h, _ptr(y), _ptr(x), int(iters),
+                                          ctypes.byref(o)))
+        return dict(schedule=o.schedule, no_tma=bool(o.no_tma), chunk=o.chunk)
 
     def apply_A(self, x):
         """A x = L x + V x in FP64 arithmetic (complex64 in and out)."""
@@ -262,3 +276,37 @@ class BatchSolver(Solver):
                 self._h, int(problem), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                 n.value, ctypes.byref(n)))
         return out
+
+
+def solve_many(solvers, ys, xs=None, tol=1e-6, maxit=10000):
+    """Solve several solvers (Solver or BatchSolver, any grids) concurrently,
+    one host thread and stream each (usp_solve_many).  Returns (xs, results)
+    with results a list per solver of per-problem result dicts."""
+    import torch
+    n = len(solvers)
+    if len(ys) != n:
+        raise ValueError("one source per solver")
+    ys = [y.contiguous() for y in ys]
+    use_x0 = xs is not None
+    if xs is None:
+        xs = [torch.empty_like(y) for y in ys]
+    counts = [getattr(s, "count", 1) for s in solvers]
+    total = sum(counts)
+    res = (Result * total)()
+    sts = (ctypes.c_int32 * total)()
+    hs = (ctypes.c_void_p * n)(*[s._h.value for s in solvers])
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    st = _lib.lib().usp_solve_many(hs, n, yp, xp, int(use_x0), float(tol), int(maxit), res,
+                                   sts)
+    check(st, (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_DIVERGED, _lib.ERR_NONFINITE))
+    out, k = [], 0
+    for c in counts:
+        lst = []
+        for _ in range(c):
+            d = res[k].as_dict()
+            d["status"] = _lib.STATUS[sts[k]]
+            lst.append(d)
+            k += 1
+        out.append(lst)
+    return xs, out

@@ -57,7 +57,9 @@ def _create(L, shape, sym=(0.0, 0.3, 0.2, -0.5), V=1, alpha=0.0, dx=1.0):
     ((4, 4, 4, 4), _lib.ERR_INVALID_ARG),       # ndim 4
     ((0, 8), _lib.ERR_INVALID_ARG),             # empty axis
     ((100,), _lib.ERR_UNSUPPORTED_SIZE),        # not a power of two
-    ((512, 2), _lib.ERR_UNSUPPORTED_SIZE),      # above 256
+    ((1024, 2), _lib.ERR_UNSUPPORTED_SIZE),     # above 512
+    ((48, 8), _lib.ERR_UNSUPPORTED_SIZE),       # 3 * 16: radix-3 lengths start at 96
+    ((768,), _lib.ERR_UNSUPPORTED_SIZE),        # 3 * 256
     ((1, 8), _lib.ERR_UNSUPPORTED_SIZE),        # length-1 axis
 ])
 def test_create_rejects_bad_grids(L, shape, expect):

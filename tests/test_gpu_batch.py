@@ -80,6 +80,8 @@ def _check_trajectories(torch, shape, probs, n_iter, vreal=False):
     ((128, 128), 3),        # staged line pass, 2 tiles per problem
     ((16, 64, 64), 2),
     ((8, 128, 128), 2),     # staged line and column passes
+    ((96, 96), 3),          # radix-3 lines
+    ((512, 64), 2),         # radix-2 outer stage on the strided axis
 ])
 def test_batch_trajectories_match_oracle(torch_cuda, shape, count):
     probs = [inputs.random_helmholtz(shape, 100 + j, sigma_px=2.0 + j,
@@ -237,3 +239,80 @@ def test_batch_apply_A_and_residual(torch_cuda):
         num += np.linalg.norm(ro) ** 2
         den += np.linalg.norm(y[j].astype(np.complex128)) ** 2
     assert rel == pytest.approx(np.sqrt(num / den), rel=1e-9)
+
+
+def _mixed_indices(per_side=2, limit=200):
+    """Indices of the mixed-size batch generator covering every side."""
+    got = {}
+    for i in range(limit):
+        n = inputs.batch_problem(i)["S"].shape[0]
+        if len(got.setdefault(n, [])) < per_side:
+            got[n].append(i)
+    assert len(got) == len(inputs.BATCH_SIDES)
+    return got
+
+
+def test_mixed_sizes_solved_concurrently(torch_cuda):
+    """Two problems of every side 64-512 (Helmholtz and diffusion), one
+    autotuned batch solver per side, all solved at once: each converged
+    field has the oracle's preconditioned residual below 1.5e-6, matches
+    the problem solved alone, and (for the sides the oracle solves quickly)
+    the oracle's own solve."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import BatchSolver, Solver, solve_many
+    dev = torch.device("cuda:0")
+    groups = _mixed_indices()
+    sides = sorted(groups)
+    probs = {n: [inputs.batch_problem(i) for i in groups[n]] for n in sides}
+    kinds = {p["kind"] for n in sides for p in probs[n]}
+    assert kinds == {"helmholtz", "diffusion"}
+    data = {}
+    for n in sides:
+        cfs = [ocanon.canonical(p) for p in probs[n]]
+        V = np.stack([cf["V"].astype(np.complex64) for cf in cfs])
+        y = np.stack([cf["y"].astype(np.complex64) for cf in cfs])
+        data[n] = (cfs, V, y)
+    solvers = [_batch(torch, (n, n), data[n][0], data[n][1]) for n in sides]
+    try:
+        ys = [torch.from_numpy(data[n][2]).to(dev) for n in sides]
+        tuned = [sv.autotune(y, iters=2) for sv, y in zip(solvers, ys)]
+        assert all(t["chunk"] >= 4 for t in tuned)
+        xs, res = solve_many(solvers, ys, tol=1e-6, maxit=20000)
+    finally:
+        for sv in solvers:
+            sv.close()
+    for gi, n in enumerate(sides):
+        cfs, V, y = data[n]
+        xg = xs[gi].cpu().numpy().astype(np.complex128)
+        for j, cf in enumerate(cfs):
+            r = res[gi][j]
+            assert r["status"] == "USP_OK" and r["converged"] == 1, (n, j, r)
+            V64, y64 = V[j].astype(np.complex128), y[j].astype(np.complex128)
+            Lh = _lh((n, n), cf)
+            d = uo.residual_delta(xg[j], y64, V64, Lh)
+            assert np.linalg.norm(d) / r["ref_norm"] < 1.5e-6, (n, j)
+            with Solver((n, n), cf["a"], cf["b"], torch.from_numpy(V[j]).to(dev)) as s1:
+                x1, r1 = s1.solve(torch.from_numpy(y[j]).to(dev), tol=1e-6, maxit=20000)
+            assert abs(r1["iterations"] - r["iterations"]) <= 2, (n, j)
+            assert _rel(xg[j], x1.cpu().numpy().astype(np.complex128)) <= 2e-6, (n, j)
+            if n <= 96:
+                xo, _, ok = uo.solve(V64, y64, Lh, r["alpha"], 1e-6, 20000)
+                assert ok and _rel(xg[j], xo) <= TOL_X, (n, j)
+
+
+def test_autotune_choice_is_cached_per_shape(torch_cuda):
+    torch = torch_cuda
+    shape = (128, 128)
+    cfs, V, y = _prep([inputs.random_helmholtz(shape, 90 + j) for j in range(2)])
+    yd = torch.from_numpy(y).to("cuda:0")
+    with _batch(torch, shape, cfs, V) as s:
+        t1 = s.autotune(yd, iters=2)
+        x, res = s.solve(yd, tol=1e-6, maxit=5000, allow_failed=False)
+    with _batch(torch, shape, cfs, V) as s:
+        t2 = s.autotune(yd, iters=2)
+    assert t1 == t2
+    assert t1["schedule"] == 1 and 4 <= t1["chunk"] <= 64
+    for j, cf in enumerate(cfs):
+        V64, y64 = V[j].astype(np.complex128), y[j].astype(np.complex128)
+        d = uo.residual_delta(x[j].cpu().numpy().astype(np.complex128), y64, V64, _lh(shape, cf))
+        assert np.linalg.norm(d) / res[j]["ref_norm"] < 1.5e-6

@@ -104,6 +104,39 @@ def test_parity_3d_shapes(torch_cuda, shape):
     _check_trajectory(torch_cuda, shape, inputs.white_helmholtz(shape, 3), 25)
 
 
+@pytest.mark.parametrize("shape", [(96,), (192,), (384,), (512,),
+                                   (96, 96), (192, 128), (384, 32), (512, 64), (64, 512),
+                                   (32, 384), (96, 8, 16), (4, 16, 384), (6 * 16, 512, 2)])
+def test_parity_radix3_and_512_lengths(torch_cuda, shape):
+    """Axis lengths 3 * 2^k and 512, transformed through the radix-3 / radix-2
+    outer stage, on every kind of pass (line pass, strided pass, both)."""
+    _check_trajectory(torch_cuda, shape, inputs.white_helmholtz(shape, 4), 25)
+
+
+def test_solve_with_refinement_radix3(torch_cuda):
+    """FP32 iteration + FP64 refinement (FP64 transforms of the same lengths)
+    on a 192 x 96 medium, to 1e-6, against the oracle's solve."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (192, 96)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 21, sigma_px=3.0, amplitude=0.3))
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev)) as s:
+        x, res = s.solve(torch.from_numpy(y).to(dev), tol=1e-6, maxit=5000,
+                         allow_not_converged=False)
+        xg = x.cpu().numpy().astype(np.complex128)
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    V64, y64 = V.astype(np.complex128), y.astype(np.complex128)
+    xo, ho, ok = uo.solve(V64, y64, Lh, res["alpha"], 1e-6, 5000)
+    assert ok and res["converged"] == 1
+    # the correction phase restarts from z = 0 at 8 tol and repeats the slow
+    # first steps of a fresh iteration: a few percent more iterations
+    assert abs(res["iterations"] - len(ho)) <= max(5, len(ho) // 20)
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL_X
+    d = uo.residual_delta(xg, y64, V64, Lh)
+    assert np.linalg.norm(d) / res["ref_norm"] < 1.5e-6
+
+
 def test_parity_3d_helmholtz_64(torch_cuda):
     """The 3-D Helmholtz medium generator at 64^3 (lengths scaled by 1/4)."""
     prob = inputs.helmholtz_3d(64, seed=0)
