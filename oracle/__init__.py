@@ -10,6 +10,8 @@ Modules:
   canon       canonical form (smallest circle, scaling) for Helmholtz and
               diffusion problems
   dense       the operators as dense matrices for brute-force checks
+  fno         the Fourier neural operator that proposes a warm start x0:
+              forward, hand-derived backward, Adam
 
 Every function pinned by a ``-m "not gpu"`` test; none is marked
 "parity unpinned".
