@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--batch-n", type=int, default=128)
     p.add_argument("--mixed", type=int, default=512,
                    help="problems of the mixed-size 2-D batch leg (0 skips it)")
+    p.add_argument("--fno-train", type=int, default=4096,
+                   help="solved 128x128 media the warm-start network trains on (0 skips)")
+    p.add_argument("--fno-epochs", type=int, default=20)
+    p.add_argument("--fno-test", type=int, default=256, help="held-out media")
     return p.parse_args()
 
 
@@ -357,7 +361,77 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
         out["batched"] = batched_leg(args, torch, dev)
     if args.mixed > 0:
         out["mixed_batch"] = mixed_batch_leg(args, torch, dev)
+    if args.fno_train > 0:
+        out["fno_warm_start"] = fno_leg(args, torch, dev)
     return out
+
+
+def fno_leg(args, torch, dev):
+    """The learned warm start on the 2-D 128x128 medium distribution: train
+    the network (width 32, 4 layers, 16 x 16 modes) on media solved by the
+    batch solver, then solve held-out media to the tolerance from zero and
+    from the network's estimate (inference included in the time)."""
+    from paper_2207_14222_gb300 import canon, inputs
+    from paper_2207_14222_gb300.fno import FNO, features
+    from paper_2207_14222_gb300.solver import BatchSolver
+    n, bs = 128, 32
+
+    def dataset(seeds):
+        probs = [inputs.helmholtz_2d(n, seed=s) for s in seeds]
+        cfs = [canon.canonical(p) for p in probs]
+        V = torch.from_numpy(np.stack([cf["V"] for cf in cfs])).to(dev)
+        y = torch.from_numpy(np.stack([cf["y"] for cf in cfs])).to(dev)
+        a = torch.from_numpy(np.stack([features(p) for p in probs])).to(dev)
+        return cfs, V, y, a
+
+    def solve(cfs, V, y, x0=None):
+        with BatchSolver((n, n), [cf["a"] for cf in cfs], [cf["b"] for cf in cfs], V) as s:
+            x, res = s.solve(y, x=x0, use_x0=x0 is not None, tol=args.tol, maxit=args.maxit)
+        return x, res
+
+    t0 = time.perf_counter()
+    cfs, V, y, a = dataset(range(10000, 10000 + args.fno_train))
+    xs, _ = solve(cfs, V, y)
+    del V, y
+    t_data = time.perf_counter() - t0
+    losses = []
+    with FNO(n, n, width=32, layers=4, modes=16, max_batch=bs, seed=0) as net:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for ep in range(args.fno_epochs):
+            perm = torch.randperm(args.fno_train, generator=torch.Generator().manual_seed(ep)).to(dev)
+            ls = [net.train_step(a[perm[k:k + bs]], xs[perm[k:k + bs]],
+                                 lr=2e-3 * 0.5 ** (ep * 3 // max(args.fno_epochs, 1)))
+                  for k in range(0, args.fno_train - bs + 1, bs)]
+            losses.append(float(np.mean(ls)))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        tcfs, tV, ty, ta = dataset(range(90000, 90000 + args.fno_test))
+        solve(tcfs, tV, ty)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xz, rz = solve(tcfs, tV, ty)
+        torch.cuda.synchronize()
+        t_zero = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        x0 = torch.cat([net.predict(ta[k:k + bs]) for k in range(0, args.fno_test, bs)])
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        xw, rw = solve(tcfs, tV, ty, x0.clone())
+        torch.cuda.synchronize()
+        t_warm = time.perf_counter() - t0
+    err = torch.linalg.vector_norm(x0 - xz, dim=(1, 2)) / torch.linalg.vector_norm(xz, dim=(1, 2))
+    iz = np.array([r["iterations"] for r in rz])
+    iw = np.array([r["iterations"] for r in rw])
+    return {"train_media": args.fno_train, "epochs": args.fno_epochs, "test_media": args.fno_test,
+            "data_s": t_data, "train_s": t_train, "loss_first_last": [losses[0], losses[-1]],
+            "median_rel_error_x0": float(err.median()),
+            "iterations_zero_median": float(np.median(iz)),
+            "iterations_warm_median": float(np.median(iw)),
+            "iterations_saved_total_frac": float(1 - iw.sum() / iz.sum()),
+            "converged_warm": int(sum(r["converged"] for r in rw)),
+            "s_zero": t_zero, "s_warm_incl_inference": t_warm, "s_inference": t_inf,
+            "speedup": t_zero / t_warm}
 
 
 def mixed_batch_leg(args, torch, dev):

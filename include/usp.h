@@ -295,6 +295,69 @@ usp_status usp_solve_noalloc(const usp_grid* grid, const usp_lsymbol* lsym, cons
                              int32_t V_is_real, double alpha, const void* y, void* x,
                              double tol, int32_t maxit, void* cuda_stream, usp_result* out);
 
+/* ---- learned initial estimate (no counterpart in the paper) -------------
+ *
+ * Algorithm 1 starts from any x0 (Sec. 2.1; the paper's examples start at
+ * 0).  This network -- a Fourier neural operator (Li et al. 2020) -- maps a
+ * description of the medium and source to an estimate of the field, which a
+ * solve then takes as x0 (use_x0 = 1, ref_norm <= 0: the stopping test keeps
+ * the alpha-free denominator ||B (L+I)^-1 y||, so the answer is the
+ * iteration's own).  Definition, per sample of c_in x h x w real inputs a:
+ *   v_0 = P a + p (per pixel);  z_l = W_l v_l + b_l + K_l v_l;
+ *   v_{l+1} = gelu(z_l) (l < layers - 1), v_layers = z_{layers-1};
+ *   K_l v = Re F^-1[S^T R_l S F v] (F the unnormalised 2-D DFT, S keeps the
+ *   modes x modes lowest frequencies: index k in [0, modes/2) or
+ *   [n - modes/2, n) per axis; R_l a complex width x width matrix per mode);
+ *   estimate = (Q v_layers + q)[0] + i (Q v_layers + q)[1];
+ *   gelu(x) = x (1 + erf(x / sqrt 2)) / 2;
+ *   loss = mean over the batch of ||estimate - x||^2 / ||x||^2.
+ * Parameters (float32, this order): P [width][c_in], p [width]; per layer
+ * W [width][width], b [width], R [width][width][modes][modes][re, im];
+ * Q [2][width], q [2].  Training: the hand-derived backward pass and Adam
+ * (beta 0.9, 0.999, eps 1e-8).  FP32 arithmetic, deterministic reductions.
+ * Inputs a: device, batch x c_in x h x w float32; fields: device, batch x h
+ * x w complex64. */
+typedef struct {
+  int32_t h, w;        /* image size, each in [8, 512]                       */
+  int32_t c_in;        /* input channels, [1, 8]                             */
+  int32_t width;       /* hidden channels, [1, 64]                           */
+  int32_t layers;      /* spectral layers, [1, 8]                            */
+  int32_t modes;       /* retained modes per axis, power of two in [2, 32]   */
+  int32_t max_batch;   /* largest batch a call may pass                      */
+} usp_fno_config;
+
+typedef struct usp_fno usp_fno;
+
+/* Number of parameters of a configuration (-1 if it is invalid). */
+int64_t usp_fno_param_count(const usp_fno_config* cfg);
+
+/* Create a network with parameters drawn from `seed` (uniform, scaled by
+ * 1/sqrt(fan-in); R by 1/width^2; biases 0) and its activation memory for
+ * max_batch samples; cuda_stream as in usp_solver_create. */
+usp_status usp_fno_create(const usp_fno_config* cfg, uint64_t seed, void* cuda_stream,
+                          usp_fno** out);
+
+/* Copy the parameters out / in (host arrays of usp_fno_param_count
+ * floats); setting them also resets the Adam state. */
+usp_status usp_fno_get_params(const usp_fno* f, float* host_out, int64_t n);
+usp_status usp_fno_set_params(usp_fno* f, const float* host_in, int64_t n);
+
+/* Field estimate for `batch` samples into x_out (device complex64). */
+usp_status usp_fno_predict(usp_fno* f, const float* a, int32_t batch, void* x_out);
+
+/* Loss against x_true (device complex64) and its gradient with respect to
+ * every parameter (host array, or NULL), without an update. */
+usp_status usp_fno_gradients(usp_fno* f, const float* a, const void* x_true,
+                             int32_t batch, float* grad_host, double* loss_out);
+
+/* One training step: forward, loss, backward, Adam update with step size
+ * lr.  *loss_out (may be NULL) receives the loss before the update. */
+usp_status usp_fno_train_step(usp_fno* f, const float* a, const void* x_true,
+                              int32_t batch, double lr, double* loss_out);
+
+/* Free a network (NULL is ignored). */
+void usp_fno_destroy(usp_fno* f);
+
 /* ---- measurement (no counterpart in the paper; used by the benchmark) -- */
 
 /* Mean duration of each kernel of one iteration. */

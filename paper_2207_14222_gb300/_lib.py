@@ -37,6 +37,11 @@ class Options(ctypes.Structure):
                 ("max_refinements", c_int32), ("no_tma", c_int32)]
 
 
+class FnoConfig(ctypes.Structure):
+    _fields_ = [("h", c_int32), ("w", c_int32), ("c_in", c_int32), ("width", c_int32),
+                ("layers", c_int32), ("modes", c_int32), ("max_batch", c_int32)]
+
+
 class PassTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", c_int32), ("ms", c_double),
                 ("bytes", c_double)]
@@ -90,6 +95,16 @@ _SIGNATURES = {
                                     _P(Result)]),
     "usp_time_passes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, _P(PassTime),
                                   c_int32, _P(c_int32)]),
+    "usp_fno_param_count": (c_int64, [_P(FnoConfig)]),
+    "usp_fno_create": (c_int32, [_P(FnoConfig), ctypes.c_uint64, c_void_p, _P(c_void_p)]),
+    "usp_fno_get_params": (c_int32, [c_void_p, _P(ctypes.c_float), c_int64]),
+    "usp_fno_set_params": (c_int32, [c_void_p, _P(ctypes.c_float), c_int64]),
+    "usp_fno_predict": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "usp_fno_gradients": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, _P(ctypes.c_float),
+                                    _P(c_double)]),
+    "usp_fno_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double,
+                                     _P(c_double)]),
+    "usp_fno_destroy": (None, [c_void_p]),
     "usp_kernel_launches": (c_int64, []),
     "usp_status_string": (ctypes.c_char_p, [c_int32]),
     "usp_last_error": (ctypes.c_char_p, []),

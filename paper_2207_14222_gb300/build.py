@@ -27,6 +27,8 @@ SOURCES = [
     "canon.cpp",
     "noalloc.cu",
     "tma_kernels.cu",
+    "fno_kernels.cu",
+    "fno_api.cpp",
 ]
 
 

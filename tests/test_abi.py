@@ -104,6 +104,21 @@ def test_batch_create_rejects_bad_arguments(L):
     assert _batch_create(L, (4, 4), [good, good]) == _lib.ERR_UNSUPPORTED_SIZE
 
 
+def test_fno_config_validation(L):
+    def count(*cfg):
+        return L.usp_fno_param_count(ctypes.byref(_lib.FnoConfig(*cfg)))
+    # P, p; per layer W, b, R (complex per mode); Q, q
+    assert count(128, 128, 3, 32, 4, 16, 8) == 32 * 3 + 32 + 4 * (32 * 32 + 32 + 32 * 32 * 256 * 2) + 64 + 2
+    assert count(128, 128, 3, 32, 4, 12, 8) == -1      # modes not a power of two
+    assert count(128, 128, 3, 65, 4, 16, 8) == -1      # width above 64
+    assert count(4, 128, 3, 8, 1, 2, 1) == -1          # image below 8
+    assert count(128, 128, 9, 8, 1, 16, 1) == -1       # too many input channels
+    h = ctypes.c_void_p()
+    assert L.usp_fno_create(ctypes.byref(_lib.FnoConfig(128, 128, 3, 8, 0, 16, 1)), 0, None,
+                            ctypes.byref(h)) == _lib.ERR_INVALID_ARG
+    L.usp_fno_destroy(None)
+
+
 def test_null_handles(L):
     r = _lib.Result()
     assert L.usp_solve(None, None, None, 0, 1e-6, 10, 0.0, ctypes.byref(r)) == _lib.ERR_INVALID_ARG
