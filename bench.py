@@ -161,12 +161,16 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# Sources of the pencil-schedule kernels whose ncu traffic is recorded.
+PENCIL_SOURCES = ("fft_core.cuh", "iteration_state.cuh", "kernels.h", "pencil_kernels.cu",
+                  "tma.cuh", "tma_kernels.cu")
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_14222_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in PENCIL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
