@@ -12,6 +12,8 @@ Modules:
   dense       the operators as dense matrices for brute-force checks
   fno         the Fourier neural operator that proposes a warm start x0:
               forward, hand-derived backward, Adam
+  variants    the block forms of Sec. 2.2 (antisymmetrised, for problems
+              that are not accretive) and Sec. 3.2 (flux form of diffusion)
 
 Every function pinned by a ``-m "not gpu"`` test; none is marked
 "parity unpinned".
