@@ -295,6 +295,72 @@ usp_status usp_solve_noalloc(const usp_grid* grid, const usp_lsymbol* lsym, cons
                              int32_t V_is_real, double alpha, const void* y, void* x,
                              double tol, int32_t maxit, void* cuda_stream, usp_result* out);
 
+/* ---- block variants of the canonical form (Sec. 2.2, Sec. 3.2) ----------
+ *
+ * The same Algorithm 1 (forward-eliminated, Sec. 2.1) on an unknown with K
+ * components per grid point, V a K x K matrix per point and L a K x K
+ * matrix of Fourier multipliers.  Fields are K consecutive planes of N =
+ * prod(n) complex64 values (component k at offset k N).  FP32 arithmetic,
+ * norms in FP64; plain Algorithm 1 (no FP64 refinement).
+ *
+ * USP_VARIANT_ANTISYMMETRIC (Sec. 2.2, Eq. antisymmetrised), K = 2: for a
+ *   raw problem A0 x0 = y0 that is not accretive, A = [[0, -A0^*], [A0, 0]]/c
+ *   with real c; x = [x0; x0'] where x0' solves the adjoint problem.  Per
+ *   point V = [[0, -conj(v)], [v, 0]]; per frequency L = [[0, -conj(l)],
+ *   [l, 0]], l = a |p|^2 + b.  params = (a_re, a_im, b_re, b_im); V: device,
+ *   N complex64 values v.  (usp_canon_antisymmetric builds them for the
+ *   Helmholtz operator.)
+ * USP_VARIANT_FLUX_DIFFUSION (Sec. 3.2, Eq. diffusion-equation-matrix-form
+ *   with d/dt = 0, scalar D(r)), K = 1 + ndim: unknown C^1/2 [u; J], per
+ *   point V = diag(Vu, VJ I), per frequency L + I = [[alpha, i s p^T],
+ *   [i s p, beta I]].  params = (alpha, beta, s), alpha, beta >= 1 (L
+ *   accretive); V: device, two planes of N float32 (Vu, then VJ).
+ *   (usp_canon_flux_diffusion builds them.)
+ * Validation: max over points of ||V|| < 1, V finite.  alpha <= 0 selects
+ * min over points of Re 1/lambda over the eigenvalues lambda of B = I - V
+ * (B is normal: 1/(1 + |v|^2) antisymmetric, 1/(1 - V) flux). */
+typedef enum {
+  USP_VARIANT_ANTISYMMETRIC = 1,
+  USP_VARIANT_FLUX_DIFFUSION = 2
+} usp_variant_kind;
+
+typedef struct usp_variant usp_variant;
+
+usp_status usp_variant_create(const usp_grid* grid, int32_t kind, const double* params,
+                              const void* V, double alpha, void* cuda_stream,
+                              usp_variant** out);
+
+/* Algorithm 1 on (y, x): device pointers, K planes each; arguments and
+ * results as usp_solve (refinements and stagnated are always 0). */
+usp_status usp_variant_solve(usp_variant* s, const void* y, void* x, int32_t use_x0,
+                             double tol, int32_t maxit, double ref_norm, usp_result* out);
+
+/* Residual history of the last solve (as usp_residual_history). */
+usp_status usp_variant_history(const usp_variant* s, double* host_out, int32_t capacity,
+                               int32_t* n_out);
+
+void usp_variant_destroy(usp_variant* s);
+
+/* Host canonical forms (FP64 in, float32/complex64 out):
+ * antisymmetrised Helmholtz laplacian psi + k^2 psi = -S (adjoint source
+ *   S_adj, NULL for none): kbar2, rho = smallest circle of the values k^2,
+ *   c = rho / norm_v (real), v = (k^2 - kbar2)/c (v_out: n complex64),
+ *   l = (-|p|^2 + kbar2)/c (params_out: 4 doubles), y = [S_adj/c; -S/c]
+ *   (y_out: 2 n complex64), c_out: 1 double.  k2, S, S_adj: n complex128.
+ * flux-form diffusion -div(D grad u) + eta u = S: etabar, Dinvbar, r_eta,
+ *   r_D = midpoints and half-ranges of eta and 1/D; c_u = r_eta/norm_v,
+ *   c_J = r_D/norm_v (a zero range takes the other's); V_out: 2 n float32
+ *   ((eta - etabar)/c_u, then (1/D - Dinvbar)/c_J); params_out: (etabar/c_u
+ *   + 1, Dinvbar/c_J + 1, 1/sqrt(c_u c_J)); y_out: (1 + ndim) n complex64,
+ *   [S/sqrt(c_u); 0]; scales_out: (c_u, c_J).  eta, D, S: n doubles
+ *   (eta >= 0, D > 0); u = x[0] / sqrt(c_u). */
+usp_status usp_canon_antisymmetric(const double* k2, const double* S, const double* S_adj,
+                                   int64_t n, double norm_v, float* v_out, float* y_out,
+                                   double* params_out, double* c_out);
+usp_status usp_canon_flux_diffusion(const double* eta, const double* D, const double* S,
+                                    int64_t n, int32_t ndim, double norm_v, float* V_out,
+                                    float* y_out, double* params_out, double* scales_out);
+
 /* ---- learned initial estimate (no counterpart in the paper) -------------
  *
  * Algorithm 1 starts from any x0 (Sec. 2.1; the paper's examples start at

@@ -105,6 +105,17 @@ _SIGNATURES = {
     "usp_fno_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double,
                                      _P(c_double)]),
     "usp_fno_destroy": (None, [c_void_p]),
+    "usp_variant_create": (c_int32, [_P(Grid), c_int32, _P(c_double), c_void_p, c_double,
+                                     c_void_p, _P(c_void_p)]),
+    "usp_variant_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
+                                    c_double, _P(Result)]),
+    "usp_variant_history": (c_int32, [c_void_p, _P(c_double), c_int32, _P(c_int32)]),
+    "usp_variant_destroy": (None, [c_void_p]),
+    "usp_canon_antisymmetric": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_double,
+                                          c_void_p, c_void_p, _P(c_double), _P(c_double)]),
+    "usp_canon_flux_diffusion": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32,
+                                           c_double, c_void_p, c_void_p, _P(c_double),
+                                           _P(c_double)]),
     "usp_kernel_launches": (c_int64, []),
     "usp_status_string": (ctypes.c_char_p, [c_int32]),
     "usp_last_error": (ctypes.c_char_p, []),

@@ -29,6 +29,8 @@ SOURCES = [
     "tma_kernels.cu",
     "fno_kernels.cu",
     "fno_api.cpp",
+    "block_kernels.cu",
+    "variant_api.cpp",
 ]
 
 

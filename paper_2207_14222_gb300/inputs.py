@@ -210,3 +210,34 @@ def batch_problem(i, seed0=1000):
     eta = 0.01 * np.exp(0.5 * g)
     return dict(kind="diffusion", eta=eta, D=1.0, S=S, dx=1.0, seed=seed0 + i,
                 sigma_px=sigma)
+
+
+def gain_helmholtz(shape, seed, contrast=0.2, gain=0.15, k0=K0_QUARTER_WAVE, sigma_px=2.0):
+    """Helmholtz medium with gain and loss: k^2 = k0^2 (n^2 + i kappa), n - 1
+    in [0, contrast] and kappa in [-gain, gain] from smoothed random fields
+    (kappa < 0: gain), so the values k^2 lie on both sides of the real axis
+    and the problem's numerical range is not confined to a half plane;
+    random complex source."""
+    rng = np.random.default_rng(seed)
+    g1 = smooth_field(shape, sigma_px, rng)
+    g2 = smooth_field(shape, sigma_px, rng)
+    n_index = 1.0 + contrast * (g1 - g1.min()) / max(g1.max() - g1.min(), 1e-30)
+    kappa = gain * (2.0 * (g2 - g2.min()) / max(g2.max() - g2.min(), 1e-30) - 1.0)
+    S = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    return dict(kind="helmholtz", k2=k0 ** 2 * (n_index ** 2 + 1j * kappa), S=S, dx=1.0,
+                k0=k0, seed=seed)
+
+
+def variable_diffusion(shape, seed, median_eta=0.05, sigma_log=0.5, d_range=(1.0, 2.0),
+                       sigma_px=2.0):
+    """Steady diffusion with a spatially varying scalar diffusion coefficient:
+    log-normal absorption eta, D uniform in d_range from a smoothed field,
+    unit point source at the centre."""
+    rng = np.random.default_rng(seed)
+    g = smooth_field(shape, sigma_px, rng)
+    eta = median_eta * np.exp(sigma_log * g)
+    h = smooth_field(shape, sigma_px, rng)
+    t = (h - h.min()) / max(h.max() - h.min(), 1e-30)
+    D = d_range[0] + (d_range[1] - d_range[0]) * t
+    return dict(kind="diffusion", eta=eta, D=D, S=_centre_point_source(shape, 1.0), dx=1.0,
+                seed=seed)

@@ -310,3 +310,82 @@ def solve_many(solvers, ys, xs=None, tol=1e-6, maxit=10000):
             k += 1
         out.append(lst)
     return xs, out
+
+
+class VariantSolver:
+    """Algorithm 1 on a block form of the canonical system (usp_variant_*):
+    kind "antisymmetric" (K = 2) or "flux" (K = 1 + ndim).  params and V as
+    returned by canon.antisymmetric / canon.flux_diffusion; V a CUDA tensor
+    (complex64 grid, or float32 (2,) + grid for the flux form)."""
+
+    KINDS = {"antisymmetric": 1, "flux": 2}
+
+    def __init__(self, shape, kind, params, V, alpha=0.0, dx=1.0, stream=None):
+        import torch
+        if not V.is_cuda:
+            raise ValueError("V must be a CUDA tensor")
+        self.shape = tuple(int(n) for n in shape)
+        self.kind = kind
+        self.K = 2 if kind == "antisymmetric" else 1 + len(self.shape)
+        V = V.contiguous()
+        self.device = V.device
+        g = Grid()
+        g.ndim = len(self.shape)
+        for i in range(3):
+            g.n[i] = self.shape[i] if i < len(self.shape) else 1
+        g.dx = float(dx)
+        p = (ctypes.c_double * 4)(*[float(v) for v in params] + [0.0] * (4 - len(params)))
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(_lib.lib().usp_variant_create(ctypes.byref(g), self.KINDS[kind], p, _ptr(V),
+                                                float(alpha), ctypes.c_void_p(stream),
+                                                ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, y, x=None, tol=1e-5, maxit=20000, ref_norm=0.0, use_x0=False,
+              allow_not_converged=True):
+        """y, x: CUDA complex64 tensors (K,) + grid; returns (x, result)."""
+        import torch
+        y = y.contiguous()
+        if x is None:
+            x = torch.empty_like(y)
+            use_x0 = False
+        res = Result()
+        allow = (_lib.OK, _lib.ERR_NOT_CONVERGED) if allow_not_converged else (_lib.OK,)
+        with torch.cuda.device(self.device):
+            st = _lib.lib().usp_variant_solve(self._h, _ptr(y), _ptr(x), int(bool(use_x0)),
+                                              float(tol), int(maxit), float(ref_norm),
+                                              ctypes.byref(res))
+        check(st, allow)
+        d = res.as_dict()
+        d["status"] = _lib.STATUS[st]
+        return x, d
+
+    def history(self):
+        n = ctypes.c_int32()
+        check(_lib.lib().usp_variant_history(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, np.float64)
+        if n.value:
+            check(_lib.lib().usp_variant_history(
+                self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                ctypes.byref(n)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().usp_variant_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -104,6 +104,27 @@ def test_batch_create_rejects_bad_arguments(L):
     assert _batch_create(L, (4, 4), [good, good]) == _lib.ERR_UNSUPPORTED_SIZE
 
 
+def test_canonical_variants_match_oracle(L):
+    from oracle import variants as ov
+    prob = inputs.gain_helmholtz((8, 12), 3)
+    Sa = inputs.random_field((8, 12), 4)
+    cp = pcanon.antisymmetric(prob["k2"], prob["S"], S_adj=Sa)
+    co = ov.antisymmetric_helmholtz(prob["k2"], prob["S"], 1.0, S_adj=Sa)
+    assert np.allclose(cp["V"], co["v"], rtol=1e-6, atol=1e-6)
+    assert np.allclose(cp["y"], co["y"], rtol=1e-6, atol=1e-6 * np.abs(co["y"]).max())
+    assert np.allclose(cp["params"], [np.real(co["a"]), np.imag(co["a"]),
+                                      np.real(co["b"]), np.imag(co["b"])], rtol=1e-12)
+    assert cp["c"] == pytest.approx(co["c"], rel=1e-12)
+    d = inputs.variable_diffusion((6, 10), 5)
+    S = np.real(d["S"])
+    fp = pcanon.flux_diffusion(d["eta"], d["D"], S)
+    fo = ov.flux_diffusion(d["eta"], d["D"], S, 1.0)
+    assert np.allclose(fp["V"][0], fo["Vu"], atol=1e-6) and np.allclose(fp["V"][1], fo["VJ"], atol=1e-6)
+    assert np.allclose(fp["params"], [fo["alpha"], fo["beta"], fo["s"]], rtol=1e-12)
+    assert np.allclose(fp["scales"], [fo["c_u"], fo["c_J"]], rtol=1e-12)
+    assert np.allclose(fp["y"], fo["y"], rtol=1e-6, atol=1e-7)
+
+
 def test_fno_config_validation(L):
     def count(*cfg):
         return L.usp_fno_param_count(ctypes.byref(_lib.FnoConfig(*cfg)))
