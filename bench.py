@@ -64,6 +64,7 @@ def parse():
                    help="solved 128x128 media the warm-start network trains on (0 skips)")
     p.add_argument("--fno-epochs", type=int, default=20)
     p.add_argument("--fno-test", type=int, default=256, help="held-out media")
+    p.add_argument("--no-variants", action="store_true", help="skip the block-variant leg")
     return p.parse_args()
 
 
@@ -367,6 +368,50 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
         out["mixed_batch"] = mixed_batch_leg(args, torch, dev)
     if args.fno_train > 0:
         out["fno_warm_start"] = fno_leg(args, torch, dev)
+    if not args.no_variants:
+        out["variants"] = variants_leg(args, torch, dev)
+    return out
+
+
+def variants_leg(args, torch, dev):
+    """The block forms: the antisymmetrised Helmholtz problem with gain on
+    256 x 256 (K = 2) and flux-form diffusion with variable D on 128^3
+    (K = 4), plain FP32 Algorithm 1 to 1e-5.  Algorithmic bytes per point
+    and iteration: pre (read K x, K y, V; write K t) + each transform pass
+    (read and write K planes) + multiply (K read, K write) + post (read K u,
+    K x, V; write K x)."""
+    from paper_2207_14222_gb300 import canon, inputs
+    from paper_2207_14222_gb300.solver import VariantSolver
+    peak, _ = measured_hbm_peak()
+    out = {}
+    cases = []
+    # the antisymmetrised form contracts slowly (its rate follows the
+    # singular values of A0, not its numerical range): a 128^2 medium with
+    # n - 1 in [0, 0.1] and |kappa| <= 0.05
+    g = inputs.gain_helmholtz((128, 128), 0, contrast=0.1, gain=0.05, sigma_px=4.0)
+    cases.append(("antisymmetric_helmholtz_128x128", (128, 128),
+                  canon.antisymmetric(g["k2"], g["S"]), 2, 8))
+    d = inputs.variable_diffusion((128, 128, 128), 0, sigma_px=4.0)
+    cases.append(("flux_diffusion_128^3", (128, 128, 128),
+                  canon.flux_diffusion(d["eta"], d["D"], np.real(d["S"])), 4, 8))
+    for name, shape, cp, K, vb in cases:
+        N = int(np.prod(shape))
+        passes = 2 * len(shape)
+        bpp = (24 * K + vb) + passes * 16 * K + 16 * K + (24 * K + vb)
+        V = torch.from_numpy(cp["V"]).to(dev)
+        y = torch.from_numpy(cp["y"]).to(dev)
+        maxit = max(args.maxit, 100000)
+        with VariantSolver(shape, cp["kind"], cp["params"], V) as s:
+            s.solve(y, tol=1e-5, maxit=50)       # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r = s.solve(y, tol=1e-5, maxit=maxit)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        gbs = bpp * N * r["iterations"] / dt / 1e9
+        out[name] = {"K": K, "iterations": r["iterations"], "converged": bool(r["converged"]),
+                     "s_to_1e-5": dt, "iter_per_s": r["iterations"] / dt,
+                     "bytes_per_point_iter": bpp, "GBps": gbs, "frac_of_peak": gbs / peak}
     return out
 
 
