@@ -68,6 +68,19 @@ def parse():
     return p.parse_args()
 
 
+def reduce_timing(elapsed_ms, units, dist, device):
+    """Whole-job timing over the ranks: the slowest rank's time and the sum
+    of the units every rank processed (identity without a process group)."""
+    if dist is None:
+        return float(elapsed_ms), int(units)
+    import torch
+    t = torch.tensor([float(elapsed_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(c.item()))
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -242,15 +255,7 @@ def run_ours(args):
     clocks = sampler.stop()
     elapsed_ms = e0.elapsed_time(e1)
     iters = sum(r["iterations"] for r in res)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        c = torch.tensor([iters], device=dev, dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        iters_all = int(c.item())
-    else:
-        iters_all = iters
+    elapsed_ms, iters_all = reduce_timing(elapsed_ms, iters, dist, dev)
     value = iters_all / (elapsed_ms / 1e3)
     ms_per_step = elapsed_ms / args.steps
 
