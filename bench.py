@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--maxit", type=int, default=20000)
     p.add_argument("--schedule", type=int, default=0)
     p.add_argument("--plain", action="store_true", help="time the plain FP32 iteration")
+    p.add_argument("--cols-tile", type=int, default=0,
+                   help="columns per staged strided-axis tile (16, 32; 0 = library default)")
     p.add_argument("--no-tma", action="store_true",
                    help="strided-axis passes without TMA staging (comparison)")
     p.add_argument("--cpu-iters", type=int, default=3)
@@ -230,7 +232,7 @@ def run_ours(args):
 
     def step():
         with Solver(shape, cf["a"], cf["b"], V, plain=args.plain, schedule=args.schedule,
-                    no_tma=args.no_tma) as s:
+                    no_tma=args.no_tma, cols_tile=args.cols_tile) as s:
             _, r = s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
         return r
 
@@ -288,6 +290,7 @@ def run_ours(args):
                 "mode": "plain" if args.plain else "fp32+fp64-refinement",
                 "schedule": ["auto", "pencil", "fused"][args.schedule],
                 "tma": not args.no_tma,
+                "cols_tile": args.cols_tile or "default",
                 "step": "create + solve to tol + destroy",
                 "l2": "inputs 384 MiB > L2, no flush",
                 "replicas": ws,
@@ -313,7 +316,8 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
     out = {}
     # per-kernel durations (CUDA events on the solver's stream) -> roofline
     xt = torch.empty_like(y)
-    with Solver(shape, cf["a"], cf["b"], V, schedule=args.schedule, no_tma=args.no_tma) as s:
+    with Solver(shape, cf["a"], cf["b"], V, schedule=args.schedule, no_tma=args.no_tma,
+                cols_tile=args.cols_tile) as s:
         s.solve(y, x=xt, tol=0.0, maxit=5)  # warm
         passes = s.time_passes(y, xt, iters=20)
     per_it_ms = sum(p["ms"] for p in passes)
@@ -528,7 +532,19 @@ def mixed_batch_leg(args, torch, dev):
         return res
 
     pts = {n: n * n for n in sides}
-    out = {"problems": args.mixed, "tol": args.tol,
+    # per side: one batched iteration's passes (CUDA events) -> roofline
+    peak, _ = measured_hbm_peak()
+    per_side = {}
+    for n in sides:
+        with BatchSolver((n, n), [cf["a"] for cf in groups[n]], [cf["b"] for cf in groups[n]],
+                         Vg[n]) as sv:
+            xt = torch.empty_like(yg[n])
+            sv.solve(yg[n], x=xt, tol=0.0, maxit=3)
+            ps = sv.time_passes(yg[n], xt, iters=10)
+        ms = sum(p["ms"] for p in ps)
+        per_side[str(n)] = {"iteration_ms": round(ms, 5),
+                            "frac": round(sum(p["bytes"] for p in ps) / (ms * 1e-3) / 1e9 / peak, 3)}
+    out = {"problems": args.mixed, "tol": args.tol, "per_side_iteration": per_side,
            "sides": {str(n): len(groups[n]) for n in sides},
            "points": int(sum(pts[n] * len(groups[n]) for n in sides)),
            "step": "create + autotune + solve every problem to tol + destroy"}
@@ -611,6 +627,18 @@ def batched_leg(args, torch, dev):
 
     out = {"problems": B, "grid": [n, n], "tol": args.tol,
            "step": "create + solve every problem to tol + destroy"}
+    # per-pass durations of one batched iteration (CUDA events) -> roofline
+    with BatchSolver((n, n), a, b, V) as s:
+        xt = torch.empty_like(y)
+        s.solve(y, x=xt, tol=0.0, maxit=3)
+        passes = s.time_passes(y, xt, iters=20)
+    peak, _ = measured_hbm_peak()
+    it_ms = sum(p["ms"] for p in passes)
+    out["roofline"] = {"iteration_ms": it_ms,
+                       "iteration_frac": sum(p["bytes"] for p in passes) / (it_ms * 1e-3) / 1e9 / peak,
+                       "passes": [{"name": p["name"], "ms": round(p["ms"], 5),
+                                   "GBps": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)}
+                                  for p in passes]}
     for name, fn in (("batched", batched), ("one_by_one", one_by_one)):
         fn()  # warm-up
         torch.cuda.synchronize()

@@ -107,6 +107,9 @@ typedef struct {
   /* 1: strided-axis passes load and store with plain global accesses
    *    instead of TMA-staged tiles (for comparison); 0: TMA (default)      */
   int32_t no_tma;
+  /* columns per staged strided-axis tile: 8, 16 or 32 (4, 2 or 1 CTAs
+   * per SM), or 0 for the library's default                                */
+  int32_t cols_tile;
 } usp_options;
 
 typedef struct usp_solver usp_solver;

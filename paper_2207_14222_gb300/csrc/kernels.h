@@ -177,7 +177,7 @@ struct ColsTmaArgs {
   Batch bt;
 };
 cudaError_t cols_tma_init();
-cudaError_t launch_cols_tma(int n, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
+cudaError_t launch_cols_tma(int n, int cols, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
                             cudaStream_t s);
 
 // Fused rows pass of the pencil schedule as a persistent, bulk-copy staged

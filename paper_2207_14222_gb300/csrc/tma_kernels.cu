@@ -1,8 +1,10 @@
 // tma_kernels.cu -- FFT passes along a strided axis with TMA-staged tiles.
 //
-// A tile is 32 consecutive columns x the whole axis (N values each), i.e. a
-// box {32, N, 1} of the field viewed as [outer][N][inner].  A persistent CTA
-// (one per SM, G = N2 warps) walks its tiles through a ring of three shared
+// A tile is COLS (32, 16 or 8) consecutive columns x the whole axis (N
+// values each), i.e. a box {COLS, N, 1} of the field viewed as
+// [outer][N][inner].  32 / COLS persistent CTAs of COLS x G threads share an
+// SM (while one waits at a barrier, the others compute); each walks its
+// tiles through a ring of three shared
 // memory slots: while tile k is transformed in its slot, the TMA loads of
 // tiles k+1 and k+2 are in flight, so the bytes in flight per SM do not
 // depend on registers.  The result is written back into the slot and stored
@@ -23,20 +25,20 @@ namespace {
 
 constexpr int SLOTS = 3;
 
-template <int N, bool INV>
+template <int N, bool INV, int COLS>
 __device__ __forceinline__ void fft_cols_slot(float2* v, float2* ex, const float2* tw, int g,
                                               int lane) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
   stage1<N, INV>(v, g, tw);
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * 32 + lane] = v[k1];
+  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * COLS + lane] = v[k1];
   __syncthreads();
   float2 w[N1];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int k1 = g + G * s;
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * 32 + lane];
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * COLS + lane];
   }
   __syncthreads();
   stage2<N, INV>(w);
@@ -61,12 +63,12 @@ __device__ __forceinline__ float axis_p2_f(const Sym<float>& s, int ax, int k) {
 
 }  // namespace
 
-template <int N>
-__global__ void __launch_bounds__(32 * Split<N>::G, 1)
+template <int N, int COLS>
+__global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
     k_cols_tma(const __grid_constant__ CUtensorMap map, const ColsTmaArgs a) {
   constexpr int N1 = Split<N>::N1, G = Split<N>::G;
-  constexpr int THREADS = 32 * G;
-  constexpr int TILE = N * 32;
+  constexpr int THREADS = COLS * G;
+  constexpr int TILE = N * COLS;
   constexpr uint32_t TILE_BYTES = TILE * sizeof(float2);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* slots = reinterpret_cast<float2*>(smem_raw);
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
   const bool batched = a.bt.count > 1;
   if (!batched && !(a.flags & F_NOSTATE) && a.st->done) return;
 
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int lane = threadIdx.x % COLS, g = threadIdx.x / COLS;
   const int64_t t0 = blockIdx.x, stride = gridDim.x;
   const int64_t my = t0 < a.tiles ? (a.tiles - t0 + stride - 1) / stride : 0;
   for (int m = threadIdx.x; m < N; m += THREADS)
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
     for (; issued < 2 && issued < my; ++issued) {
       const int64_t t = t0 + issued * stride;
       mbar_arrive_expect_tx(&full[issued], TILE_BYTES);
-      tma_load_3d(slots + issued * TILE, &map, int((t % a.inner_blocks) * 32), 0,
+      tma_load_3d(slots + issued * TILE, &map, int((t % a.inner_blocks) * COLS), 0,
                   int(t / a.inner_blocks), &full[issued]);
     }
   }
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
     }
     float2* slot = slots + s * TILE;
     const int64_t t = t0 + k * stride;
-    const int64_t col = (t % a.inner_blocks) * 32 + lane;
+    const int64_t col = (t % a.inner_blocks) * COLS + lane;
     // batch: the tile's problem; a finished problem's tiles are left as they are
     const int pb = batched ? int((t / a.inner_blocks) / a.bt.outer_per) : 0;
     const bool skip = batched && !(a.flags & F_NOSTATE) && a.st[pb].done;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
           const int s2 = int(issued % SLOTS);
           const int64_t t2 = t0 + issued * stride;
           mbar_arrive_expect_tx(&full[s2], TILE_BYTES);
-          tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * 32), 0,
+          tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * COLS), 0,
                       int(t2 / a.inner_blocks), &full[s2]);
           ++issued;
         }
@@ -141,12 +143,12 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
     const float b1 = sy.b_re + 1.f;
     float2 v[N1];
 #pragma unroll
-    for (int q = 0; q < N1; ++q) v[q] = slot[in_index<N>(g, q) * 32 + lane];
+    for (int q = 0; q < N1; ++q) v[q] = slot[in_index<N>(g, q) * COLS + lane];
     __syncthreads();  // the slot now serves as the exchange buffer
     if (a.mode == COL_INV) {
-      fft_cols_slot<N, true>(v, slot, tw, g, lane);
+      fft_cols_slot<N, true, COLS>(v, slot, tw, g, lane);
     } else {
-      fft_cols_slot<N, false>(v, slot, tw, g, lane);
+      fft_cols_slot<N, false, COLS>(v, slot, tw, g, lane);
       if (a.mode == COL_FWD_MUL_INV) {
         // outermost axis: the column index holds the faster axes' frequencies
         float p2in = 0.f;
@@ -177,15 +179,15 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
         out_to_in<N>(v, tmp);
 #pragma unroll
         for (int q = 0; q < N1; ++q) v[q] = tmp[q];
-        fft_cols_slot<N, true>(v, slot, tw, g, lane);
+        fft_cols_slot<N, true, COLS>(v, slot, tw, g, lane);
       }
     }
 #pragma unroll
-    for (int q = 0; q < N1; ++q) slot[out_index<N>(g, q) * 32 + lane] = v[q];
+    for (int q = 0; q < N1; ++q) slot[out_index<N>(g, q) * COLS + lane] = v[q];
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
-      tma_store_3d(&map, int((t % a.inner_blocks) * 32), 0, int(t / a.inner_blocks), slot);
+      tma_store_3d(&map, int((t % a.inner_blocks) * COLS), 0, int(t / a.inner_blocks), slot);
       bulk_commit();
       if (issued < my) {
         // the slot of tile k+2 held tile k-1, whose store was committed one
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(32 * Split<N>::G, 1)
         const int s2 = int(issued % SLOTS);
         const int64_t t2 = t0 + issued * stride;
         mbar_arrive_expect_tx(&full[s2], TILE_BYTES);
-        tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * 32), 0,
+        tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * COLS), 0,
                     int(t2 / a.inner_blocks), &full[s2]);
         ++issued;
       }
@@ -473,22 +475,28 @@ cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t 
   }
 }
 
-template <int N>
+template <int N, int COLS>
 static size_t cols_tma_smem() {
-  return sizeof(float2) * (SLOTS * N * 32 + N);
+  return sizeof(float2) * (SLOTS * N * COLS + N);
 }
 
-template <int N>
+template <int N, int COLS>
 static cudaError_t cols_tma_go(const CUtensorMap& map, const ColsTmaArgs& a, int grid,
                                cudaStream_t s) {
-  k_cols_tma<N><<<grid, 32 * Split<N>::G, cols_tma_smem<N>(), s>>>(map, a);
+  k_cols_tma<N, COLS><<<grid, COLS * Split<N>::G, cols_tma_smem<N, COLS>(), s>>>(map, a);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t cols_tma_attr() {
-  return cudaFuncSetAttribute(k_cols_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)cols_tma_smem<N>());
+  cudaError_t e = cudaFuncSetAttribute(k_cols_tma<N, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cols_tma_smem<N, 32>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cols_tma<N, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cols_tma_smem<N, 16>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cols_tma<N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)cols_tma_smem<N, 8>());
 }
 
 cudaError_t cols_tma_init() {
@@ -503,19 +511,24 @@ cudaError_t cols_tma_init() {
   return cols_tma_attr<256>();
 }
 
-cudaError_t launch_cols_tma(int n, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
-                            cudaStream_t s) {
+cudaError_t launch_cols_tma(int n, int cols, const CUtensorMap& map, const ColsTmaArgs& a,
+                            int grid, cudaStream_t s) {
+#define C_(N)                                                        \
+  (cols == 8 ? cols_tma_go<N, 8>(map, a, grid, s)                     \
+             : (cols == 16 ? cols_tma_go<N, 16>(map, a, grid, s) : cols_tma_go<N, 32>(map, a, grid, s)))
+  if (cols != 8 && cols != 16 && cols != 32) return cudaErrorInvalidValue;
   switch (n) {
-    case 2: return cols_tma_go<2>(map, a, grid, s);
-    case 4: return cols_tma_go<4>(map, a, grid, s);
-    case 8: return cols_tma_go<8>(map, a, grid, s);
-    case 16: return cols_tma_go<16>(map, a, grid, s);
-    case 32: return cols_tma_go<32>(map, a, grid, s);
-    case 64: return cols_tma_go<64>(map, a, grid, s);
-    case 128: return cols_tma_go<128>(map, a, grid, s);
-    case 256: return cols_tma_go<256>(map, a, grid, s);
+    case 2: return C_(2);
+    case 4: return C_(4);
+    case 8: return C_(8);
+    case 16: return C_(16);
+    case 32: return C_(32);
+    case 64: return C_(64);
+    case 128: return C_(128);
+    case 256: return C_(256);
     default: return cudaErrorInvalidValue;
   }
+#undef C_
 }
 
 }  // namespace usp

@@ -135,8 +135,12 @@ struct usp_solver {
   std::vector<std::vector<double>> histories;   // per problem, last solve
   int num_sms = 0;
   bool maps_ok = false;            // TMA tensor maps of the scratch field
-  CUtensorMap map_ax[2];           // [axis]: strided-axis views of s->buf (axis 0, axis 1)
+  CUtensorMap map_ax[3][2];        // [tile 32 / 16 / 8 columns][axis]: strided-axis views of s->buf
 };
+
+// Column-tile width of the staged strided-axis passes when the options leave
+// it to the library.
+static constexpr int kDefaultColsTile = 8;
 
 static bool is_pow2_in_range(int64_t v) { return v >= 2 && v <= 256 && (v & (v - 1)) == 0; }
 // Axis lengths the line kernels transform: 2^k in [2, 256], and 3 * 2^k or
@@ -166,12 +170,13 @@ static bool tensor_map_encoder() {
 }
 
 // The field viewed as [outer][n][inner] complex64 (8-byte elements), tiles of
-// {32, n, 1}.
-static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, int64_t outer) {
+// {cols, n, 1}.
+static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, int64_t outer,
+                            int cols) {
   if (!tensor_map_encoder()) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)n, (cuuint64_t)outer};
   const cuuint64_t strides[2] = {(cuuint64_t)inner * 8, (cuuint64_t)n * inner * 8};
-  const cuuint32_t box[3] = {32, (cuuint32_t)n, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)n, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -188,7 +193,9 @@ static void build_maps(usp_solver* s) {
     int64_t inner = 1, outer = 1;
     for (int ax = axis + 1; ax < s->ndim; ++ax) inner *= s->n[ax];
     for (int ax = 0; ax < axis; ++ax) outer *= s->n[ax];
-    ok = ok && encode_cols_map(&s->map_ax[axis], s->buf, inner, s->n[axis], outer * s->B);
+    ok = ok && encode_cols_map(&s->map_ax[0][axis], s->buf, inner, s->n[axis], outer * s->B, 32);
+    ok = ok && encode_cols_map(&s->map_ax[1][axis], s->buf, inner, s->n[axis], outer * s->B, 16);
+    ok = ok && encode_cols_map(&s->map_ax[2][axis], s->buf, inner, s->n[axis], outer * s->B, 8);
   }
   s->maps_ok = ok;
 }
@@ -251,19 +258,21 @@ static std::function<cudaError_t(cudaStream_t)> cols_pass_f32(usp_solver* s, int
   auto c = cols_args<float>(s, axis, mode, MUL_LINV, flags, s->buf, s->symf);
   const int n = s->n[axis];
   if (s->maps_ok && !s->opt.no_tma) {
+    // tiles of 32 / 16 / 8 columns run 1 / 2 / 4 CTAs per SM
+    const int cols = s->opt.cols_tile ? s->opt.cols_tile : kDefaultColsTile;
     ColsTmaArgs t{};
     t.mode = mode;
     t.mul = MUL_LINV;
     t.flags = flags;
-    t.inner_blocks = c.inner_blocks;
-    t.tiles = c.inner_blocks * c.outer;
+    t.inner_blocks = (c.inner + cols - 1) / cols;
+    t.tiles = t.inner_blocks * c.outer;
     t.st = s->st;
     t.tw = s->tw32;
     t.sym = s->symf;
     t.bt = c.bt;
-    const int grid = (int)std::min<int64_t>(t.tiles, s->num_sms);
-    const CUtensorMap map = s->map_ax[axis];
-    return [=](cudaStream_t st) { return launch_cols_tma(n, map, t, grid, st); };
+    const int grid = (int)std::min<int64_t>(t.tiles, (int64_t)s->num_sms * (32 / cols));
+    const CUtensorMap map = s->map_ax[cols == 32 ? 0 : (cols == 16 ? 1 : 2)][axis];
+    return [=](cudaStream_t st) { return launch_cols_tma(n, cols, map, t, grid, st); };
   }
   return [=](cudaStream_t st) { return launch_cols_f32(n, c, st); };
 }
@@ -733,6 +742,8 @@ extern "C" usp_status usp_batch_create(const usp_grid* grid, int32_t count,
 
 extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* opt) {
   if (!s || !opt) return fail(USP_ERR_INVALID_ARG, "NULL argument");
+  if (opt->cols_tile != 0 && opt->cols_tile != 8 && opt->cols_tile != 16 && opt->cols_tile != 32)
+    return fail(USP_ERR_INVALID_ARG, "cols_tile must be 0, 8, 16 or 32");
   if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 2)
     return fail(USP_ERR_INVALID_ARG, "invalid option value");
   if (opt->schedule == 2 && !fused_supported(s))
@@ -1316,12 +1327,14 @@ extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_
   const int nx = s->n[s->ndim - 1];
   const bool staged = s->maps_ok || nx == 128 || nx == 256;
   for (int sched = 1; sched <= (fused_supported(s) ? 2 : 1); ++sched)
-    for (int nt = 0; nt <= (staged ? 1 : 0); ++nt) {
-      usp_options o = s->opt;
-      o.schedule = sched;
-      o.no_tma = nt;
-      cands.push_back(o);
-    }
+    for (int nt = 0; nt <= (staged ? 1 : 0); ++nt)
+      for (int ct = (s->maps_ok && nt == 0 ? 8 : 16); ct <= (s->maps_ok && nt == 0 ? 32 : 16); ct *= 2) {
+        usp_options o = s->opt;
+        o.schedule = sched;
+        o.no_tma = nt;
+        o.cols_tile = ct;
+        cands.push_back(o);
+      }
   const usp_options keep = s->opt;
   double best_ms = 1e300;
   for (const usp_options& o : cands) {

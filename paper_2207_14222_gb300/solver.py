@@ -38,7 +38,7 @@ class Solver:
     """
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
-                 schedule=0, chunk=0, max_refinements=0, no_tma=False):
+                 schedule=0, chunk=0, max_refinements=0, no_tma=False, cols_tile=0):
         import torch
         L = _lib.lib()
         if not V.is_cuda:
@@ -66,11 +66,12 @@ class Solver:
                                       ctypes.c_void_p(stream), ctypes.byref(h)))
         self._h = h
         self.set_options(plain=plain, schedule=schedule, chunk=chunk,
-                         max_refinements=max_refinements, no_tma=no_tma)
+                         max_refinements=max_refinements, no_tma=no_tma, cols_tile=cols_tile)
 
-    def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False):
+    def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False,
+                    cols_tile=0):
         o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements),
-                    int(bool(no_tma)))
+                    int(bool(no_tma)), int(cols_tile))
         check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
 
     @property
@@ -143,7 +144,8 @@ class Solver:
         with torch.cuda.device(self.device):
             check(_lib.lib().usp_autotune(self._h, _ptr(y), _ptr(x), int(iters),
                                           ctypes.byref(o)))
-        return dict(schedule=o.schedule, no_tma=bool(o.no_tma), chunk=o.chunk)
+        return dict(schedule=o.schedule, no_tma=bool(o.no_tma), chunk=o.chunk,
+                    cols_tile=o.cols_tile)
 
     def apply_A(self, x):
         """A x = L x + V x in FP64 arithmetic (complex64 in and out)."""
