@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--plain", action="store_true", help="time the plain FP32 iteration")
     p.add_argument("--cols-tile", type=int, default=0,
                    help="columns per staged strided-axis tile (16, 32; 0 = library default)")
+    p.add_argument("--tc-dft", action="store_true",
+                   help="256-point strided-axis transforms on the tensor cores")
     p.add_argument("--no-tma", action="store_true",
                    help="strided-axis passes without TMA staging (comparison)")
     p.add_argument("--cpu-iters", type=int, default=3)
@@ -232,7 +234,7 @@ def run_ours(args):
 
     def step():
         with Solver(shape, cf["a"], cf["b"], V, plain=args.plain, schedule=args.schedule,
-                    no_tma=args.no_tma, cols_tile=args.cols_tile) as s:
+                    no_tma=args.no_tma, cols_tile=args.cols_tile, tc_dft=args.tc_dft) as s:
             _, r = s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
         return r
 
@@ -291,6 +293,7 @@ def run_ours(args):
                 "schedule": ["auto", "pencil", "fused"][args.schedule],
                 "tma": not args.no_tma,
                 "cols_tile": args.cols_tile or "default",
+                "tc_dft": args.tc_dft,
                 "step": "create + solve to tol + destroy",
                 "l2": "inputs 384 MiB > L2, no flush",
                 "replicas": ws,
@@ -317,7 +320,7 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
     # per-kernel durations (CUDA events on the solver's stream) -> roofline
     xt = torch.empty_like(y)
     with Solver(shape, cf["a"], cf["b"], V, schedule=args.schedule, no_tma=args.no_tma,
-                cols_tile=args.cols_tile) as s:
+                cols_tile=args.cols_tile, tc_dft=args.tc_dft) as s:
         s.solve(y, x=xt, tol=0.0, maxit=5)  # warm
         passes = s.time_passes(y, xt, iters=20)
     per_it_ms = sum(p["ms"] for p in passes)

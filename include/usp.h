@@ -110,6 +110,10 @@ typedef struct {
   /* columns per staged strided-axis tile: 8, 16 or 32 (4, 2 or 1 CTAs
    * per SM), or 0 for the library's default                                */
   int32_t cols_tile;
+  /* 1: the 256-point transforms of the strided-axis passes run on the
+   *    tensor cores (tcgen05, TF32 split into three products for FP32-level
+   *    accuracy; single problems, pencil schedule); 0: CUDA cores           */
+  int32_t tc_dft;
 } usp_options;
 
 typedef struct usp_solver usp_solver;

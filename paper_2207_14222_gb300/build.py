@@ -31,6 +31,7 @@ SOURCES = [
     "fno_api.cpp",
     "block_kernels.cu",
     "variant_api.cpp",
+    "tc_kernels.cu",
 ]
 
 

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "tc_kernels.h"
 #include "usp.h"
 
 using namespace usp;
@@ -76,6 +77,7 @@ static usp_status ensure_device_init() {
   CUDA_TRY(plane_kernel_init());
   CUDA_TRY(cols_tma_init());
   CUDA_TRY(rows_tma_init());
+  CUDA_TRY(tc_cols_init());
   if (dev < 64) g_init_mask |= (1ull << dev);
   return USP_OK;
 }
@@ -257,6 +259,22 @@ static std::function<cudaError_t(cudaStream_t)> cols_pass_f32(usp_solver* s, int
                                                               int flags) {
   auto c = cols_args<float>(s, axis, mode, MUL_LINV, flags, s->buf, s->symf);
   const int n = s->n[axis];
+  if (s->opt.tc_dft && n == 256 && s->B == 1 && !(flags & F_CBLOCK) && s->maps_ok && !s->opt.no_tma) {
+    // the 256-point transforms on the tensor cores (tiles of 8 columns)
+    ColsTmaArgs t{};
+    t.mode = mode;
+    t.mul = MUL_LINV;
+    t.flags = flags;
+    t.inner_blocks = (c.inner + 7) / 8;
+    t.tiles = t.inner_blocks * c.outer;
+    t.st = s->st;
+    t.tw = s->tw32;
+    t.sym = s->symf;
+    t.bt = c.bt;
+    const int grid = (int)std::min<int64_t>(t.tiles, (int64_t)s->num_sms * 2);
+    const CUtensorMap map = s->map_ax[2][axis];
+    return [=](cudaStream_t st) { return launch_cols_tc(map, t, grid, st); };
+  }
   if (s->maps_ok && !s->opt.no_tma) {
     // tiles of 32 / 16 / 8 columns run 1 / 2 / 4 CTAs per SM
     const int cols = s->opt.cols_tile ? s->opt.cols_tile : kDefaultColsTile;

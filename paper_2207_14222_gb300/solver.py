@@ -38,7 +38,8 @@ class Solver:
     """
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
-                 schedule=0, chunk=0, max_refinements=0, no_tma=False, cols_tile=0):
+                 schedule=0, chunk=0, max_refinements=0, no_tma=False, cols_tile=0,
+                 tc_dft=False):
         import torch
         L = _lib.lib()
         if not V.is_cuda:
@@ -66,12 +67,13 @@ class Solver:
                                       ctypes.c_void_p(stream), ctypes.byref(h)))
         self._h = h
         self.set_options(plain=plain, schedule=schedule, chunk=chunk,
-                         max_refinements=max_refinements, no_tma=no_tma, cols_tile=cols_tile)
+                         max_refinements=max_refinements, no_tma=no_tma, cols_tile=cols_tile,
+                         tc_dft=tc_dft)
 
     def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False,
-                    cols_tile=0):
+                    cols_tile=0, tc_dft=False):
         o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements),
-                    int(bool(no_tma)), int(cols_tile))
+                    int(bool(no_tma)), int(cols_tile), int(bool(tc_dft)))
         check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
 
     @property

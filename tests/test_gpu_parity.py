@@ -42,13 +42,13 @@ def _prep(prob, vreal=False):
     return cf, V, y
 
 
-def _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha=0.0, schedule=0):
+def _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha=0.0, schedule=0, **opts):
     from paper_2207_14222_gb300.solver import Solver
     dev = torch.device("cuda:0")
     Vd = torch.from_numpy(V).to(dev)
     yd = torch.from_numpy(y).to(dev)
     with Solver(shape, cf["a"], cf["b"], Vd, alpha=alpha, dx=cf["dx"], plain=True,
-                schedule=schedule) as s:
+                schedule=schedule, **opts) as s:
         x, res = s.solve(yd, tol=0.0, maxit=n_iter)
         hist = s.history()
         torch.cuda.synchronize()
@@ -60,16 +60,17 @@ def _oracle_iterate(shape, cf, V, y, n_iter, alpha):
     return uo.iterate(V.astype(np.complex128), y.astype(np.complex128), Lh, alpha, n_iter)
 
 
-def _check_trajectory(torch, shape, prob, n_iter, vreal=False, alpha=0.0, schedule=0):
+def _check_trajectory(torch, shape, prob, n_iter, vreal=False, alpha=0.0, schedule=0,
+                      tol_x=TOL_X, **opts):
     cf, V, y = _prep(prob, vreal)
-    xg, res, hg = _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha, schedule)
+    xg, res, hg = _gpu_iterate(torch, shape, cf, V, y, n_iter, alpha, schedule, **opts)
     assert res["iterations"] == n_iter
     a = res["alpha"]
     if alpha <= 0:
         assert a == pytest.approx(uo.alpha_star(V.astype(np.complex128)), rel=1e-6)
     xo, ho = _oracle_iterate(shape, cf, V, y, n_iter, a)
     err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
-    assert err <= TOL_X, err
+    assert err <= tol_x, err
     far = ho > 1e-3
     herr = np.max(np.abs(hg[far] - ho[far]) / ho[far])
     assert herr <= TOL_HIST, herr
@@ -206,6 +207,48 @@ def test_parity_full_size_256_bench_configuration(torch_cuda):
     shape = (256, 256, 256)
     prob = inputs.helmholtz_3d(256, seed=0)
     _check_trajectory(torch_cuda, shape, prob, 3)
+
+
+# The TF32 three-product split rounds each 16-point stage at about twice
+# FP32's error, so the raw trajectory gets 5e-5; the path's bar (1e-5 to the
+# oracle) applies after refinement, in the converged-solve test below.
+TOL_TC = 5e-5
+
+
+@pytest.mark.parametrize("shape", [(256, 64), (256, 8, 32), (256, 256, 16)])
+def test_parity_tensor_core_dft(torch_cuda, shape):
+    """The 256-point strided-axis transforms on the tensor cores (TF32 split
+    into three products): the oracle's trajectory on 2-D and 3-D grids (one
+    or both strided axes of length 256)."""
+    _check_trajectory(torch_cuda, shape, inputs.random_helmholtz(shape, 31), 25,
+                      tol_x=TOL_TC, tc_dft=True)
+
+
+def test_parity_tensor_core_dft_bench_configuration(torch_cuda):
+    shape = (256, 256, 256)
+    _check_trajectory(torch_cuda, shape, inputs.helmholtz_3d(256, seed=0), 3, tol_x=TOL_TC,
+                      tc_dft=True)
+
+
+def test_tensor_core_dft_solve_with_refinement(torch_cuda):
+    """To 1e-6 with the tensor-core transforms and FP64 refinement: the
+    oracle's preconditioned residual of the result is below 1.5e-6."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (256, 128)
+    cf, V, y = _prep(inputs.random_helmholtz(shape, 32, sigma_px=4.0))
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), tc_dft=True) as s:
+        x, res = s.solve(torch.from_numpy(y).to(dev), tol=1e-6, maxit=20000,
+                         allow_not_converged=False)
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    xg = x.cpu().numpy().astype(np.complex128)
+    V64, y64 = V.astype(np.complex128), y.astype(np.complex128)
+    d = uo.residual_delta(xg, y64, V64, Lh)
+    assert np.linalg.norm(d) / res["ref_norm"] < 1.5e-6
+    # the tensor-core path's bar: within 1e-5 of the oracle's solve after refinement
+    xo, _, ok = uo.solve(V64, y64, Lh, res["alpha"], 1e-6, 20000)
+    assert ok and np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL_X
 
 
 # ------------------------------------------------------ full solves ---
