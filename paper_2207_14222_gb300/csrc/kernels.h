@@ -162,6 +162,7 @@ cudaError_t plane_kernel_init();
 cudaError_t launch_plane(const PlaneArgs& a, int clusters, cudaStream_t s);
 int plane_max_active_clusters();
 const float2* twiddle_table_f32();
+const float2* twiddle_x_table_f32();   // W_1536^m, m < 1536
 
 // Strided-axis pass with TMA-staged tiles (tma_kernels.cu).  The tensor map
 // views the field as [outer][N][inner] (3-D, 8-byte elements, box {32, N, 1}).
@@ -191,6 +192,7 @@ struct RowsTmaArgs {
   const void* V;
   float2* buf;
   const float2* tw;     // W_256^m table (device)
+  const float2* twx;    // W_1536^m table (device): radix stage of 96..512
   double* partials;     // one double per CTA (single problem) or per tile (batch)
   DevState* st;
   double* hist;
@@ -198,6 +200,9 @@ struct RowsTmaArgs {
   Batch bt;
 };
 cudaError_t rows_tma_init();
+// Rows per tile of the staged rows pass for rows of length n (0: no staged
+// kernel for this length).
+int rows_tma_tile_rows(int n);
 cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s);
 
 // Launchers (pencil_kernels.cu).  n = transform length (power of two, 2..256).

@@ -584,6 +584,12 @@ static cudaError_t attrs_all() {
 
 // Twiddles from the first octant by symmetry, so W^(64 j) are exactly
 // 1, -i, -1, i and the table is exactly symmetric.
+const float2* twiddle_x_table_f32() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_twx32) != cudaSuccess) return nullptr;
+  return reinterpret_cast<const float2*>(p);
+}
+
 const float2* twiddle_table_f32() {
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_tw32) != cudaSuccess) return nullptr;

@@ -249,18 +249,48 @@ __device__ __forceinline__ void fft_rows_slot(float2* v, float2* exr, const floa
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
+// Block shape of the staged rows pass: G line threads per row (Line<N>),
+// 512 threads (384 for radix-3 lines, so that whole rows fill the block).
 template <int N>
-__global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
-  constexpr int N1 = Split<N>::N1, G = Split<N>::G;
-  constexpr int F = 512 / G;            // rows per tile
+struct RowsTma {
+  static constexpr int THREADS = Line<N>::R == 3 ? 384 : 512;
+  static constexpr int F = THREADS / Line<N>::G;   // rows per tile
+  static_assert(F * Line<N>::G == THREADS, "rows must fill the block");
+};
+
+// Line transforms of one row held by G threads, exchange in the row's N
+// values of a slot (radix stage over the whole row, M-point transforms on
+// the sub-rows).
+template <int N>
+__device__ __forceinline__ void line_inv_slot(float2* v, float2* exr, const float2* tw,
+                                              const float2* rtw, int l) {
+  typedef Line<N> L;
+  radix_inv<N, 1>(v, exr, rtw, l, 0);
+  fft_rows_slot<L::M, true>(v, exr + (l / L::GM) * L::M, tw, l % L::GM);
+}
+template <int N>
+__device__ __forceinline__ void line_fwd_slot(float2* v, float2* exr, const float2* tw,
+                                              const float2* rtw, int l) {
+  typedef Line<N> L;
+  fft_rows_slot<L::M, false>(v, exr + (l / L::GM) * L::M, tw, l % L::GM);
+  radix_fwd<N, 1>(v, exr, rtw, l, 0);
+}
+
+template <int N>
+__global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsTmaArgs a) {
+  typedef Line<N> L;
+  constexpr int N1 = L::NV, G = L::G, M = L::M;
+  constexpr int THREADS = RowsTma<N>::THREADS;
+  constexpr int F = RowsTma<N>::F;      // rows per tile
   constexpr int TILE = F * N;           // complex values per tile
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* SU = reinterpret_cast<float2*>(smem_raw);
   float2* SV = SU + TILE;
   float2* SY = SV + TILE;
-  float2* tw = SY + TILE;
+  float2* tw = SY + TILE;               // M-point stage-1 twiddles
+  float2* rtw = tw + M;                 // W_N^m (radix stage), R > 1
   __shared__ __align__(8) uint64_t bars[3];   // U, V, Y slots
-  __shared__ double red[16];
+  __shared__ double red[THREADS / 32];
   __shared__ int is_last, ok_flag;
 
   const bool batched = a.bt.count > 1;
@@ -278,8 +308,10 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
     for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
   }
-  for (int m = tid; m < N; m += 512)
-    tw[m] = a.tw[stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N)];
+  for (int m = tid; m < M; m += THREADS)
+    tw[m] = a.tw[stage1_twiddle_exponent(m, Split<M>::N2) * (256 / M)];
+  if (L::R > 1)
+    for (int m = tid; m < N; m += THREADS) rtw[m] = a.twx[m * (1536 / N)];
   __syncthreads();
 
   auto first_row = [&](int64_t k) { return (t0 + k * stride) * F; };
@@ -313,12 +345,12 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
   };
 
   float2 xr[N1];
-  auto prefetch_x = [&](int64_t k) {    // this thread's x at points out_index(g, q)
+  auto prefetch_x = [&](int64_t k) {    // this thread's x at points L::sp_out(g, q)
     const int64_t row = first_row(k) + f;
     const bool act = row < a.nrows && !xzero;
 #pragma unroll
     for (int q = 0; q < N1; ++q)
-      xr[q] = act ? a.x_in[row * N + out_index<N>(g, q)] : make_float2(0.f, 0.f);
+      xr[q] = act ? a.x_in[row * N + L::sp_out(g, q)] : make_float2(0.f, 0.f);
   };
 
   if (tid == 0 && my > 0) {
@@ -340,10 +372,10 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
     float2 v[N1];
 #pragma unroll
     for (int q = 0; q < N1; ++q)
-      v[q] = act ? SU[f * N + in_index<N>(g, q)] : make_float2(0.f, 0.f);
+      v[q] = act ? SU[f * N + L::fr_in(g, q)] : make_float2(0.f, 0.f);
     __syncthreads();
     // inverse FFT along x, exchange in the U slot, which is then refilled
-    fft_rows_slot<N, true>(v, SU + f * N, tw, g);
+    line_inv_slot<N>(v, SU + f * N, tw, rtw, g);
     release_then(0, k + 1);
     wait_bar(1, par);
     wait_bar(2, par);
@@ -351,7 +383,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
     const float al = batched && a.bt.alpha ? a.bt.alpha[pb] : a.alpha;
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
-      const int c = f * N + out_index<N>(g, q);
+      const int c = f * N + L::sp_out(g, q);
       const float2 vv = vreal ? make_float2(reinterpret_cast<const float*>(SV)[c], 0.f) : SV[c];
       const float2 yv = SY[c];
       const float br = 1.f - vv.x, bi = -vv.y;
@@ -360,7 +392,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
       const float2 xn = make_float2(xr[q].x + al * dr, xr[q].y + al * di);
       if (act) {
         acc += dr * dr + di * di;
-        a.x_out[row * N + out_index<N>(g, q)] = xn;
+        a.x_out[row * N + L::sp_out(g, q)] = xn;
       }
       v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
     }
@@ -370,17 +402,18 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
     // refilled; the output index set equals the input set, so the registers
     // are reordered once into the stage-1 order
     float2 t[N1];
-    out_to_in<N>(v, t);
+    out_to_in<M>(v, t);
 #pragma unroll
     for (int q = 0; q < N1; ++q) v[q] = t[q];
-    fft_rows_slot<N, false>(v, SY + f * N, tw, g);
+    line_fwd_slot<N>(v, SY + f * N, tw, rtw, g);
     if (act) {
 #pragma unroll
-      for (int q = 0; q < N1; ++q) a.buf[row * N + out_index<N>(g, q)] = v[q];
+      for (int q = 0; q < N1; ++q) a.buf[row * N + L::fr_out(g, q)] = v[q];
     }
     release_then(2, k + 1);
     if (batched && !pdone) {
-      // per-tile partial; the last tile of the problem finalises it
+      // per-tile partial of ||Delta||^2 (the problems are finalised once, at
+      // the end of the kernel)
       double dv = (double)acc;
       acc = 0.f;
 #pragma unroll
@@ -389,19 +422,8 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
       __syncthreads();
       if (tid == 0) {
         double bs = 0.0;
-        for (int i = 0; i < 16; ++i) bs += red[i];
-        const int64_t tg = t0 + k * stride, tpp = a.bt.rows_per / F;
-        a.partials[tg] = bs;
-        __threadfence();
-        const unsigned tk = atomicAdd(&a.st[pb].ticket, 1u);
-        if (tk == (unsigned)(tpp - 1)) {
-          __threadfence();
-          double tot = 0.0;
-          for (int64_t i = 0; i < tpp; ++i) tot += __ldcg(a.partials + pb * tpp + i);
-          if (a.st[pb].status != ST_TIMEOUT)
-            finalize_iteration(a.st + pb, a.hist + (int64_t)pb * a.bt.hist_stride, tot, a.flags);
-          a.st[pb].ticket = 0u;
-        }
+        for (int i = 0; i < THREADS / 32; ++i) bs += red[i];
+        a.partials[t0 + k * stride] = bs;
       }
       __syncthreads();
     }
@@ -413,7 +435,30 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
       a.st[q].done = 1;
     }
   }
-  if (batched) return;
+  if (batched) {
+    // The last CTA to finish sums each running problem's tile partials in
+    // tile order (deterministic), one thread per problem, and updates its
+    // state; one grid-wide ticket (problem 0's) per launch.
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      is_last = atomicAdd(&a.st[0].ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const int64_t tpp = a.bt.rows_per / F;
+    for (int pb = tid; pb < a.bt.count; pb += THREADS) {   // one thread per problem
+      if (__ldcg(&a.st[pb].done)) continue;   // its tiles were skipped
+      double sm = 0.0;
+      for (int64_t i = 0; i < tpp; ++i) sm += __ldcg(a.partials + pb * tpp + i);
+      if (a.st[pb].status != ST_TIMEOUT)
+        finalize_iteration(a.st + pb, a.hist + (int64_t)pb * a.bt.hist_stride, sm, a.flags);
+    }
+    __syncthreads();
+    if (tid == 0) a.st[0].ticket = 0u;
+    return;
+  }
   // ||Delta||^2: block partial, the last block finalises (fixed order)
   double dv = (double)acc;
 #pragma unroll
@@ -422,7 +467,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
   __syncthreads();
   if (tid == 0) {
     double bs = 0.0;
-    for (int i = 0; i < 16; ++i) bs += red[i];
+    for (int i = 0; i < THREADS / 32; ++i) bs += red[i];
     a.partials[blockIdx.x] = bs;
     __threadfence();
     const unsigned tk = atomicAdd(&a.st->ticket, 1u);
@@ -432,7 +477,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
   if (is_last) {
     __threadfence();
     double sm = 0.0;
-    for (unsigned i = tid; i < gridDim.x; i += 512) sm += __ldcg(a.partials + i);
+    for (unsigned i = tid; i < gridDim.x; i += THREADS) sm += __ldcg(a.partials + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sm += __shfl_down_sync(0xffffffffu, sm, o);
     __syncthreads();
@@ -440,7 +485,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
     __syncthreads();
     if (tid == 0) {
       double tot = 0.0;
-      for (int i = 0; i < 16; ++i) tot += red[i];
+      for (int i = 0; i < THREADS / 32; ++i) tot += red[i];
       if (a.st->status != ST_TIMEOUT) finalize_iteration(a.st, a.hist, tot, a.flags);
       a.st->ticket = 0u;
     }
@@ -449,28 +494,51 @@ __global__ void __launch_bounds__(512, 1) k_rows_tma(const RowsTmaArgs a) {
 
 template <int N>
 static size_t rows_tma_smem() {
-  constexpr int F = 512 / Split<N>::G;
-  return sizeof(float2) * (3 * F * N + N);
+  return sizeof(float2) * (3 * RowsTma<N>::F * N + Line<N>::M + (Line<N>::R > 1 ? N : 0));
 }
 
 template <int N>
 static cudaError_t rows_tma_go(const RowsTmaArgs& a, int grid, cudaStream_t s) {
-  k_rows_tma<N><<<grid, 512, rows_tma_smem<N>(), s>>>(a);
+  k_rows_tma<N><<<grid, RowsTma<N>::THREADS, rows_tma_smem<N>(), s>>>(a);
   return cudaGetLastError();
 }
 
+template <int N>
+static cudaError_t rows_tma_attr() {
+  return cudaFuncSetAttribute(k_rows_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rows_tma_smem<N>());
+}
+
 cudaError_t rows_tma_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_rows_tma<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)rows_tma_smem<256>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_rows_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)rows_tma_smem<128>());
+  cudaError_t e;
+  if ((e = rows_tma_attr<96>()) != cudaSuccess) return e;
+  if ((e = rows_tma_attr<128>()) != cudaSuccess) return e;
+  if ((e = rows_tma_attr<192>()) != cudaSuccess) return e;
+  if ((e = rows_tma_attr<256>()) != cudaSuccess) return e;
+  if ((e = rows_tma_attr<384>()) != cudaSuccess) return e;
+  return rows_tma_attr<512>();
+}
+
+int rows_tma_tile_rows(int n) {
+  // 96 and 192: the plain line pass is faster (tiles of 16-32 short rows
+  // leave too little work between the slot hand-offs)
+  switch (n) {
+    case 128: return RowsTma<128>::F;
+    case 256: return RowsTma<256>::F;
+    case 384: return RowsTma<384>::F;
+    case 512: return RowsTma<512>::F;
+    default: return 0;
+  }
 }
 
 cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s) {
   switch (n) {
-    case 256: return rows_tma_go<256>(a, grid, s);
+    case 96: return rows_tma_go<96>(a, grid, s);
     case 128: return rows_tma_go<128>(a, grid, s);
+    case 192: return rows_tma_go<192>(a, grid, s);
+    case 256: return rows_tma_go<256>(a, grid, s);
+    case 384: return rows_tma_go<384>(a, grid, s);
+    case 512: return rows_tma_go<512>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -378,9 +378,9 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
     const double bytes = 32.0 + vb + (xz ? 0.0 : 8.0);
     // bulk copies read y, V and the scratch field: 16-byte aligned sources
     const bool aligned = (((uintptr_t)y | (uintptr_t)s->V | (uintptr_t)s->buf) & 15u) == 0;
-    const int64_t tile_rows = nx == 256 ? 32 : 64;
-    const bool tiles_fit = s->B == 1 || (r.bt.rows_per % tile_rows) == 0;
-    if (!s->opt.no_tma && aligned && tiles_fit && (nx == 128 || nx == 256)) {
+    const int64_t tile_rows = rows_tma_tile_rows(nx);
+    const bool tiles_fit = tile_rows > 0 && (s->B == 1 || (r.bt.rows_per % tile_rows) == 0);
+    if (!s->opt.no_tma && aligned && tiles_fit) {
       RowsTmaArgs t{};
       t.flags = r.flags;
       t.nrows = r.nrows;
@@ -390,6 +390,7 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
       t.V = s->V;
       t.buf = s->buf;
       t.tw = s->tw32;
+      t.twx = twiddle_x_table_f32();
       t.partials = s->partials;
       t.st = s->st;
       t.hist = s->hist;
@@ -676,9 +677,9 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   CREATE_TRY(cudaMalloc(&s->V, vbytes));
   CREATE_TRY(cudaMalloc(&s->buf, sizeof(float2) * (size_t)NB));
   const int64_t g32 = rows_grid_f32(s), g64 = rows_grid_f64(s);
-  // one per block of the rows passes, two per FP64 block, one per 32-line
-  // tile of the staged rows pass, three per statistics block
-  s->npartials = std::max<int64_t>({g32, 2 * g64, NB / s->n[s->ndim - 1] / 32 + 1, 3 * 1024, 64});
+  // one per block of the rows passes, two per FP64 block, one per tile
+  // (at least 16 lines) of the staged rows pass, three per statistics block
+  s->npartials = std::max<int64_t>({g32, 2 * g64, NB / s->n[s->ndim - 1] / 16 + 1, 3 * 1024, 64});
   CREATE_TRY(cudaMalloc(&s->partials, sizeof(double) * s->npartials));
   CREATE_TRY(cudaMalloc(&s->st, sizeof(DevState) * count));
   CREATE_TRY(cudaMallocHost(&s->st_host, sizeof(DevState) * count));
@@ -1343,7 +1344,7 @@ extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_
   // candidates: pass schedule x staged (TMA) or plain loads
   std::vector<usp_options> cands;
   const int nx = s->n[s->ndim - 1];
-  const bool staged = s->maps_ok || nx == 128 || nx == 256;
+  const bool staged = s->maps_ok || rows_tma_tile_rows(nx) > 0;
   for (int sched = 1; sched <= (fused_supported(s) ? 2 : 1); ++sched)
     for (int nt = 0; nt <= (staged ? 1 : 0); ++nt)
       for (int ct = (s->maps_ok && nt == 0 ? 8 : 16); ct <= (s->maps_ok && nt == 0 ? 32 : 16); ct *= 2) {
