@@ -97,21 +97,36 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
 #pragma unroll
   for (int q = 0; q < N1; ++q) pz2[q] = mul ? axis_p2_f(a.sym, 0, out_index<N>(g, q)) : 0.f;
 
-  int64_t issued = 0;  // tiles whose loads were issued (thread 0 only)
-  if (threadIdx.x == 0) {
-    for (; issued < 2 && issued < my; ++issued) {
-      const int64_t t = t0 + issued * stride;
-      mbar_arrive_expect_tx(&full[issued], TILE_BYTES);
-      tma_load_3d(slots + issued * TILE, &map, int((t % a.inner_blocks) * COLS), 0,
-                  int(t / a.inner_blocks), &full[issued]);
-    }
-  }
+  // The CTA walks its tiles k (tile t0 + k stride) in order, skipping the
+  // tiles of finished problems of a batch (their done flags do not change
+  // during the pass): no loads are issued for them.  j counts the tiles
+  // walked, which sets the ring slot and the barrier phase.
+  auto active = [&](int64_t kk) {
+    if (!batched || (a.flags & F_NOSTATE)) return true;
+    const int64_t tt = t0 + kk * stride;
+    return !a.st[int((tt / a.inner_blocks) / a.bt.outer_per)].done;
+  };
+  auto next_active = [&](int64_t kk) {
+    do ++kk; while (kk < my && !active(kk));
+    return kk;
+  };
+  auto issue = [&](int64_t kk, int64_t jj) {   // thread 0: tile kk into slot jj
+    const int sl = int(jj % SLOTS);
+    const int64_t tt = t0 + kk * stride;
+    mbar_arrive_expect_tx(&full[sl], TILE_BYTES);
+    tma_load_3d(slots + sl * TILE, &map, int((tt % a.inner_blocks) * COLS), 0,
+                int(tt / a.inner_blocks), &full[sl]);
+  };
 
-  int64_t k = 0;
+  int64_t ik = next_active(-1), ij = 0;   // next tile to load and its walk index (thread 0)
+  if (threadIdx.x == 0)
+    for (; ij < 2 && ik < my; ++ij, ik = next_active(ik)) issue(ik, ij);
+
+  int64_t k = next_active(-1), j = 0;
   bool failed = false;
-  for (; k < my; ++k) {
-    const int s = int(k % SLOTS);
-    if (threadIdx.x == 0) ok_flag = mbar_wait(&full[s], uint32_t((k / SLOTS) & 1)) ? 1 : 0;
+  for (; k < my; k = next_active(k), ++j) {
+    const int s = int(j % SLOTS);
+    if (threadIdx.x == 0) ok_flag = mbar_wait(&full[s], uint32_t((j / SLOTS) & 1)) ? 1 : 0;
     __syncthreads();
     if (!ok_flag) {
       failed = true;
@@ -120,25 +135,7 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
     float2* slot = slots + s * TILE;
     const int64_t t = t0 + k * stride;
     const int64_t col = (t % a.inner_blocks) * COLS + lane;
-    // batch: the tile's problem; a finished problem's tiles are left as they are
     const int pb = batched ? int((t / a.inner_blocks) / a.bt.outer_per) : 0;
-    const bool skip = batched && !(a.flags & F_NOSTATE) && a.st[pb].done;
-    if (skip) {
-      __syncthreads();  // every thread has seen the slot state before it is reloaded
-      if (threadIdx.x == 0) {
-        bulk_commit();  // empty group: one group per tile keeps the slot accounting
-        if (issued < my) {
-          bulk_wait_read<1>();
-          const int s2 = int(issued % SLOTS);
-          const int64_t t2 = t0 + issued * stride;
-          mbar_arrive_expect_tx(&full[s2], TILE_BYTES);
-          tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * COLS), 0,
-                      int(t2 / a.inner_blocks), &full[s2]);
-          ++issued;
-        }
-      }
-      continue;
-    }
     const Sym<float> sy = problem_sym(a.sym, a.bt, pb);
     const float b1 = sy.b_re + 1.f;
     float2 v[N1];
@@ -189,16 +186,13 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
     if (threadIdx.x == 0) {
       tma_store_3d(&map, int((t % a.inner_blocks) * COLS), 0, int(t / a.inner_blocks), slot);
       bulk_commit();
-      if (issued < my) {
-        // the slot of tile k+2 held tile k-1, whose store was committed one
-        // tile ago: wait until at most the newest group still reads
+      if (ik < my) {
+        // the slot of walk position j+2 held position j-1, whose store was
+        // committed one tile ago: wait until at most the newest group reads
         bulk_wait_read<1>();
-        const int s2 = int(issued % SLOTS);
-        const int64_t t2 = t0 + issued * stride;
-        mbar_arrive_expect_tx(&full[s2], TILE_BYTES);
-        tma_load_3d(slots + s2 * TILE, &map, int((t2 % a.inner_blocks) * COLS), 0,
-                    int(t2 / a.inner_blocks), &full[s2]);
-        ++issued;
+        issue(ik, ij);
+        ++ij;
+        ik = next_active(ik);
       }
     }
   }
@@ -206,7 +200,7 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
     bulk_wait<0>();
     if (failed) {
       // let the loads still in flight land before the CTA's shared memory goes
-      for (int64_t j = k; j < issued; ++j) mbar_wait(&full[j % SLOTS], uint32_t((j / SLOTS) & 1));
+      for (int64_t p = j; p < ij; ++p) mbar_wait(&full[p % SLOTS], uint32_t((p / SLOTS) & 1));
       for (int q = 0; q < (batched ? a.bt.count : 1); ++q) {
         a.st[q].status = ST_TIMEOUT;
         a.st[q].done = 1;
@@ -353,21 +347,30 @@ __global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsT
       xr[q] = act ? a.x_in[row * N + L::sp_out(g, q)] : make_float2(0.f, 0.f);
   };
 
-  if (tid == 0 && my > 0) {
-    issue(0, 0);
-    issue(1, 0);
-    issue(2, 0);
+  // The CTA walks its tiles in order, skipping the tiles of finished
+  // problems of a batch (their done flags do not change during the pass), so
+  // no copies are issued for them; the walk index j sets the barrier phase.
+  auto active = [&](int64_t kk) { return !batched || !a.st[int(first_row(kk) / a.bt.rows_per)].done; };
+  auto next_active = [&](int64_t kk) {
+    do ++kk; while (kk < my && !active(kk));
+    return kk;
+  };
+  const int64_t k_first = next_active(-1);
+  if (tid == 0 && k_first < my) {
+    issue(0, k_first);
+    issue(1, k_first);
+    issue(2, k_first);
   }
-  if (my > 0) prefetch_x(0);
+  if (k_first < my) prefetch_x(k_first);
 
   float acc = 0.f;
-  for (int64_t k = 0; k < my; ++k) {
-    const uint32_t par = uint32_t(k & 1);
+  int64_t j = 0;
+  for (int64_t k = k_first; k < my; ++j) {
+    const int64_t kn = next_active(k);
+    const uint32_t par = uint32_t(j & 1);
     const int64_t row = first_row(k) + f;
-    // batch: the tile's problem; a finished problem's tiles change nothing
     const int pb = batched ? int(first_row(k) / a.bt.rows_per) : 0;
-    const bool pdone = batched && a.st[pb].done;
-    const bool act = row < a.nrows && !pdone;
+    const bool act = row < a.nrows;
     wait_bar(0, par);
     float2 v[N1];
 #pragma unroll
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsT
     __syncthreads();
     // inverse FFT along x, exchange in the U slot, which is then refilled
     line_inv_slot<N>(v, SU + f * N, tw, rtw, g);
-    release_then(0, k + 1);
+    release_then(0, kn);
     wait_bar(1, par);
     wait_bar(2, par);
     // Delta = (1-V)(u - x); x += alpha Delta; next t = (1-V) x + y
@@ -396,8 +399,8 @@ __global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsT
       }
       v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
     }
-    release_then(1, k + 1);
-    if (k + 1 < my) prefetch_x(k + 1);
+    release_then(1, kn);
+    if (kn < my) prefetch_x(kn);
     // forward FFT along x, exchange in the Y slot (consumed), which is then
     // refilled; the output index set equals the input set, so the registers
     // are reordered once into the stage-1 order
@@ -410,8 +413,8 @@ __global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsT
 #pragma unroll
       for (int q = 0; q < N1; ++q) a.buf[row * N + L::fr_out(g, q)] = v[q];
     }
-    release_then(2, k + 1);
-    if (batched && !pdone) {
+    release_then(2, kn);
+    if (batched) {
       // per-tile partial of ||Delta||^2 (the problems are finalised once, at
       // the end of the kernel)
       double dv = (double)acc;
@@ -427,6 +430,7 @@ __global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsT
       }
       __syncthreads();
     }
+    k = kn;
   }
 
   if (!ok && tid == 0) {
