@@ -68,12 +68,27 @@ typedef struct {
   double dx;
 } usp_grid;
 
-/* Fourier symbol of L:  Lhat(p) = a |p|^2 + b  (complex a, b).
- * Helmholtz (Sec. 3.1, Eq. laplacian_inverse): a = -1/c, b = kbar2/c.
- * Diffusion (Sec. 3.2, scalar D, steady state): a = D/c, b = etabar/c. */
+/* Fourier symbol of L (Sec. 2: L translation invariant, so F L F^-1 is a
+ * multiplication by Lhat(p)).
+ * USP_LSYM_QUADRATIC (kind 0, the default of a zero-initialised struct):
+ *   Lhat(p) = a |p|^2 + b  (complex a, b).
+ *   Helmholtz (Sec. 3.1, Eq. laplacian_inverse): a = -1/c, b = kbar2/c.
+ *   Diffusion (Sec. 3.2, scalar D, steady state): a = D/c, b = etabar/c.
+ * USP_LSYM_TABLE (kind 1): Lhat given point by point in k-space: `table`
+ *   is a device pointer to N complex64 values in the grid's layout (C order,
+ *   last axis fastest), entry (m0, m1, m2) for the FFT-order frequency
+ *   indices m_ax (0 .. n_ax - 1; index m stands for m or m - n_ax).  Any
+ *   translation-invariant L (a finite-difference Laplacian, anisotropic or
+ *   dispersive operators) fits.  Copied at create; Re(Lhat + 1) > 0 and
+ *   finiteness are checked there.  Single-problem solvers only (batches and
+ *   usp_solve_noalloc take the quadratic kind); a, b are ignored. */
+typedef enum { USP_LSYM_QUADRATIC = 0, USP_LSYM_TABLE = 1 } usp_lsym_kind;
+
 typedef struct {
   double a_re, a_im;
   double b_re, b_im;
+  int32_t kind;        /* usp_lsym_kind */
+  const void* table;   /* USP_LSYM_TABLE: device, N complex64 */
 } usp_lsymbol;
 
 /* Outcome of a solve (valid for USP_OK and USP_ERR_NOT_CONVERGED). */

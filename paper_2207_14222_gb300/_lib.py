@@ -20,7 +20,8 @@ class Grid(ctypes.Structure):
 
 
 class LSymbol(ctypes.Structure):
-    _fields_ = [("a_re", c_double), ("a_im", c_double), ("b_re", c_double), ("b_im", c_double)]
+    _fields_ = [("a_re", c_double), ("a_im", c_double), ("b_re", c_double), ("b_im", c_double),
+                ("kind", c_int32), ("table", c_void_p)]
 
 
 class Result(ctypes.Structure):

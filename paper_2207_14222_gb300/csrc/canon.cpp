@@ -117,6 +117,8 @@ extern "C" usp_status usp_canon_helmholtz(const double* k2, const double* S, int
   lsym_out->a_im = a.imag();
   lsym_out->b_re = b.real();
   lsym_out->b_im = b.imag();
+  lsym_out->kind = USP_LSYM_QUADRATIC;
+  lsym_out->table = nullptr;
   if (c_out) {
     c_out[0] = c.real();
     c_out[1] = c.imag();
@@ -152,6 +154,8 @@ extern "C" usp_status usp_canon_diffusion(const double* eta, double D, const dou
   lsym_out->a_im = 0.0;
   lsym_out->b_re = etabar / c;
   lsym_out->b_im = 0.0;
+  lsym_out->kind = USP_LSYM_QUADRATIC;
+  lsym_out->table = nullptr;
   if (c_out) {
     c_out[0] = c;
     c_out[1] = 0.0;

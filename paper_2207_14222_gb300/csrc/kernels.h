@@ -85,7 +85,18 @@ struct Sym {
   T ks[3];        // 2 pi / (n_ax dx) per axis (axis 0 slowest)
   int n[3];
   int ndim;
+  const float2* table;   // Lhat per k-space point (C order), or nullptr: a |p|^2 + b
 };
+
+// k-space linear index of frequency index k along axis 0 and the flat
+// index `col` over the faster axes (natural order, or the column-block
+// layout col = (cb * 256 + ky) * 32 + xl of the fused schedule).
+template <typename T>
+__host__ __device__ __forceinline__ int64_t kspace_index(const Sym<T>& s, int k, int64_t col, bool cblock) {
+  const int64_t inner = s.ndim == 3 ? (int64_t)s.n[1] * s.n[2] : (s.ndim == 2 ? s.n[1] : 1);
+  if (cblock) col = ((col >> 5) & 255) * 256 + (col >> 13) * 32 + (col & 31);
+  return (int64_t)k * inner + col;
+}
 
 // Independent problems on the same grid, stacked along a new slowest axis.
 // count == 1 is the single-problem solver (the kernels then use the scalar
@@ -220,6 +231,9 @@ cudaError_t init_twiddles();
 // their reduction into out[3] (device).
 cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials,
                            int nblocks, double* out, cudaStream_t s);
+// A symbol table's min Re(Lhat) + 1 and non-finite count into out[0..1].
+cudaError_t launch_table_stats(const float2* table, int64_t n, double* partials, int nblocks,
+                               double* out, cudaStream_t s);
 // x += z (complex64); with `mask` (per problem, n_per points each) only where
 // mask[problem] != 0.
 cudaError_t launch_axpy1(float2* x, const float2* z, int64_t n, cudaStream_t s,

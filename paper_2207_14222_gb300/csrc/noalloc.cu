@@ -177,6 +177,10 @@ extern "C" usp_status usp_solve_noalloc(const usp_grid* grid, const usp_lsymbol*
     set_last_error("usp_solve_noalloc: maxit %d exceeds the fixed limit %d", maxit, kMaxIters);
     return USP_ERR_INVALID_ARG;
   }
+  if (lsym->kind != USP_LSYM_QUADRATIC) {
+    set_last_error("usp_solve_noalloc: only the quadratic symbol is supported (kind %d)", (int)lsym->kind);
+    return USP_ERR_INVALID_ARG;
+  }
   Ctx c{};
   c.ndim = grid->ndim;
   c.N = 1;

@@ -145,6 +145,16 @@ __device__ __forceinline__ V spectral_factor(T p2, const Sym<T>& s, int mul) {
   return mkc<V>(dr * sc, -li * sc);
 }
 
+// The same factors from a tabulated symbol value l = Lhat(p).
+template <typename T, typename V>
+__device__ __forceinline__ V table_factor(float2 l, const Sym<T>& s, int mul) {
+  const T lr = T(l.x), li = T(l.y);
+  if (mul == MUL_L) return mkc<V>(lr * s.inv_n, li * s.inv_n);
+  const T dr = lr + T(1);
+  const T sc = quot(s.inv_n, dr * dr + li * li);
+  return mkc<V>(dr * sc, -li * sc);
+}
+
 // |p|^2 contributed by axis `ax` at frequency index k.
 template <typename T>
 __device__ __forceinline__ T axis_p2(const Sym<T>& s, int ax, int k) {
@@ -260,7 +270,8 @@ __global__ void __launch_bounds__(RowsShape<T, N>::THREADS, RowsShape<T, N>::MIN
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       const int k = L::fr_out(g, q);
-      v[q] = cmul(v[q], spectral_factor<T, V>(axis_p2(sy, 0, k), sy, a.mul));
+      v[q] = cmul(v[q], sy.table ? table_factor<T, V>(sy.table[k], sy, a.mul)
+                                 : spectral_factor<T, V>(axis_p2(sy, 0, k), sy, a.mul));
     }
   }
   if (a.mode & R_INV) {
@@ -450,7 +461,10 @@ __global__ void __launch_bounds__(ColsShape<N>::THREADS) k_cols(const ColsArgs<T
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
         const int k = L::fr_out(g, q);
-        v[q] = cmul(v[q], spectral_factor<T, V>(p2in + axis_p2(sy, 0, k), sy, a.mul));
+        v[q] = cmul(v[q], sy.table
+                              ? table_factor<T, V>(sy.table[kspace_index(sy, k, col, (a.flags & F_CBLOCK) != 0)],
+                                                   sy, a.mul)
+                              : spectral_factor<T, V>(p2in + axis_p2(sy, 0, k), sy, a.mul));
       }
       out_to_in<M>(v, t);
 #pragma unroll
@@ -718,6 +732,59 @@ cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials
                            double* out, cudaStream_t s) {
   k_v_stats<<<nblocks, 256, 0, s>>>(V, vreal, n, partials);
   k_v_stats_final<<<1, 256, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+// min over the table of Re(Lhat) + 1 and the count of non-finite entries.
+__global__ void k_table_stats(const float2* t, int64_t n, double* partials) {
+  float rmin = 3.0e38f;
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 l = t[i];
+    if (!isfinite(l.x) || !isfinite(l.y)) {
+      ++bad;
+      continue;
+    }
+    rmin = fminf(rmin, l.x + 1.f);
+  }
+  __shared__ float r0[8];
+  __shared__ int r1[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmin = fminf(rmin, __shfl_down_sync(0xffffffffu, rmin, o));
+    bad += __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r0[threadIdx.x >> 5] = rmin;
+    r1[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      r0[0] = fminf(r0[0], r0[i]);
+      r1[0] += r1[i];
+    }
+    partials[2 * blockIdx.x] = r0[0];
+    partials[2 * blockIdx.x + 1] = r1[0];
+  }
+}
+
+__global__ void k_table_stats_final(const double* partials, int nb, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double rmin = 1e300, bad = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    rmin = fmin(rmin, partials[2 * b]);
+    bad += partials[2 * b + 1];
+  }
+  out[0] = rmin;
+  out[1] = bad;
+}
+
+cudaError_t launch_table_stats(const float2* table, int64_t n, double* partials, int nblocks,
+                               double* out, cudaStream_t s) {
+  k_table_stats<<<nblocks, 256, 0, s>>>(table, n, partials);
+  k_table_stats_final<<<1, 32, 0, s>>>(partials, nblocks, out);
   return cudaGetLastError();
 }
 

@@ -250,9 +250,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         const float b1 = sy.b_re + 1.f;
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
-          const float p2 = p2in + p2_axis(sy, 0, hq + 16 * k2);
-          const float dr = fmaf(sy.a_re, p2, b1);
-          const float di = fmaf(sy.a_im, p2, sy.b_im);
+          float dr, di;
+          if (sy.table) {   // tabulated symbol
+            const float2 l = sy.table[kspace_index(sy, hq + 16 * k2, gcol, false)];
+            dr = l.x + 1.f;
+            di = l.y;
+          } else {
+            const float p2 = p2in + p2_axis(sy, 0, hq + 16 * k2);
+            dr = fmaf(sy.a_re, p2, b1);
+            di = fmaf(sy.a_im, p2, sy.b_im);
+          }
           const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, di * di));
           v[k2] = cmul(v[k2], make_float2(dr * sc, -di * sc));
         }

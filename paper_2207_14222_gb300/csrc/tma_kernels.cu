@@ -56,6 +56,13 @@ __device__ __forceinline__ float2 spectral_factor_f(float p2, const Sym<float>& 
   return make_float2(dr * sc, -li * sc);
 }
 
+__device__ __forceinline__ float2 table_factor_f(float2 l, const Sym<float>& s, int mul) {
+  if (mul == MUL_L) return make_float2(l.x * s.inv_n, l.y * s.inv_n);
+  const float dr = l.x + 1.f;
+  const float sc = __fdividef(s.inv_n, dr * dr + l.y * l.y);
+  return make_float2(dr * sc, -l.y * sc);
+}
+
 __device__ __forceinline__ float axis_p2_f(const Sym<float>& s, int ax, int k) {
   const float p = s.ks[ax] * float(signed_freq(k, s.n[ax]));
   return p * p;
@@ -158,7 +165,14 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
           p2in = axis_p2_f(sy, 1, int(col));
         }
         float2 tmp[N1];
-        if (a.mul == MUL_LINV) {
+        if (sy.table) {
+          // tabulated symbol: one lookup per point
+#pragma unroll
+          for (int q = 0; q < N1; ++q)
+            v[q] = cmul(v[q], table_factor_f(sy.table[kspace_index(sy, out_index<N>(g, q), col,
+                                                                   (a.flags & F_CBLOCK) != 0)],
+                                             sy, a.mul));
+        } else if (a.mul == MUL_LINV) {
           // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
 #pragma unroll
           for (int q = 0; q < N1; ++q) {

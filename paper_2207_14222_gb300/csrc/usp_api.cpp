@@ -133,6 +133,7 @@ struct usp_solver {
   float* balpha = nullptr;         // per-problem steps (B > 1), device
   int* bmask = nullptr;            // problems refined in the current phase, device
   int* bmask_host = nullptr;       // pinned mirror
+  float2* table = nullptr;         // tabulated symbol Lhat(p) (USP_LSYM_TABLE), device
   std::vector<double> alphas;      // per problem
   std::vector<std::vector<double>> histories;   // per problem, last solve
   int num_sms = 0;
@@ -575,6 +576,7 @@ static void destroy_impl(usp_solver* s) {
   cudaFree(s->balpha);
   cudaFree(s->bmask);
   cudaFreeHost(s->bmask_host);
+  cudaFree(s->table);
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream) cudaStreamDestroy(s->stream);
   cudaSetDevice(cur);
@@ -605,6 +607,16 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   }
   for (int p = 0; p < count; ++p) {
     const usp_lsymbol* lsym = lsyms + p;
+    if (lsym->kind == USP_LSYM_TABLE) {
+      // checked on the device after the copy (Re(Lhat + 1) > 0, finite)
+      if (count != 1) return fail(USP_ERR_INVALID_ARG, "a tabulated symbol is single-problem only");
+      if (!lsym->table) return fail(USP_ERR_INVALID_ARG, "USP_LSYM_TABLE needs a non-NULL table");
+      if (std::isnan(alphas[p]) || std::isinf(alphas[p]) || alphas[p] > 2.0)
+        return fail(USP_ERR_ALPHA_RANGE, "alpha must be finite and in (0, 2] (or <= 0 for automatic)");
+      continue;
+    }
+    if (lsym->kind != USP_LSYM_QUADRATIC)
+      return fail(USP_ERR_INVALID_ARG, "unknown symbol kind %d (problem %d)", (int)lsym->kind, p);
     const double sv[4] = {lsym->a_re, lsym->a_im, lsym->b_re, lsym->b_im};
     for (double v : sv)
       if (!std::isfinite(v)) return fail(USP_ERR_INVALID_ARG, "symbol coefficients must be finite (problem %d)", p);
@@ -694,6 +706,25 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   CREATE_TRY(cudaStreamWaitEvent(s->stream, s->ev, 0));
   CREATE_TRY(launch_copy_bytes(s->V, V, vbytes, s->stream));
   const int nb = (int)std::min<int64_t>(1024, (N + 255) / 256);
+  if (lsym->kind == USP_LSYM_TABLE) {
+    CREATE_TRY(cudaMalloc(&s->table, sizeof(float2) * (size_t)N));
+    CREATE_TRY(launch_copy_bytes(s->table, lsym->table, sizeof(float2) * (size_t)N, s->stream));
+    CREATE_TRY(launch_table_stats(s->table, N, s->partials, nb, s->red, s->stream));
+    g_launches.fetch_add(3);
+    CREATE_TRY(cudaMemcpyAsync(s->red_host, s->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CREATE_TRY(cudaStreamSynchronize(s->stream));
+    const double remin = s->red_host[0], bad = s->red_host[1];
+    if (bad > 0) {
+      destroy_impl(s);
+      return fail(USP_ERR_NONFINITE, "the symbol table holds %.0f non-finite values", bad);
+    }
+    if (!(remin > 0.0)) {
+      destroy_impl(s);
+      return fail(USP_ERR_NOT_ACCRETIVE, "Re(Lhat(p)+1) = %.6g <= 0 in the symbol table", remin);
+    }
+    s->symf.table = s->table;
+    s->symd.table = s->table;
+  }
   s->alphas.assign(count, 0.0);
   for (int p = 0; p < count; ++p) {
     const void* Vp = static_cast<const char*>(s->V) + esz * (size_t)N * p;

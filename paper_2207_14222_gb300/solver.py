@@ -39,7 +39,10 @@ class Solver:
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
                  schedule=0, chunk=0, max_refinements=0, no_tma=False, cols_tile=0,
-                 tc_dft=False):
+                 tc_dft=False, lhat_table=None):
+        """Lhat(p) = a |p|^2 + b, or, with `lhat_table` (a complex64 CUDA tensor of the
+        grid's shape, k-space in FFT order), the tabulated symbol; a and b are then
+        ignored."""
         import torch
         L = _lib.lib()
         if not V.is_cuda:
@@ -57,6 +60,14 @@ class Solver:
             g.n[i] = self.shape[i] if i < len(self.shape) else 1
         g.dx = float(dx)
         sym = LSymbol(complex(a).real, complex(a).imag, complex(b).real, complex(b).imag)
+        if lhat_table is not None:
+            if (not lhat_table.is_cuda or lhat_table.dtype != torch.complex64
+                    or tuple(lhat_table.shape) != self.shape):
+                raise ValueError("lhat_table must be a complex64 CUDA tensor of shape %s"
+                                 % (self.shape,))
+            lhat_table = lhat_table.contiguous()
+            sym.kind = 1
+            sym.table = _ptr(lhat_table)
         if stream is None:
             stream = torch.cuda.current_stream(self.device).cuda_stream
         self._stream = stream

@@ -79,6 +79,32 @@ def test_create_rejects_bad_arguments(L):
     assert "alpha" in _lib.last_error()
 
 
+def test_table_symbol_rejections(L):
+    """A tabulated symbol needs a table, one problem, and a known kind; the
+    allocation-free entry point takes the quadratic symbol only."""
+    g = _grid((8, 8))
+    h = ctypes.c_void_p()
+    s = _lib.LSymbol(0.0, 0.0, 0.0, 0.0, 1, None)          # kind TABLE, NULL table
+    assert L.usp_solver_create(ctypes.byref(g), ctypes.byref(s), ctypes.c_void_p(1), 0, 0.0,
+                               None, ctypes.byref(h)) == _lib.ERR_INVALID_ARG
+    assert "table" in _lib.last_error()
+    s = _lib.LSymbol(0.0, 0.3, 0.2, -0.5, 7, None)         # unknown kind
+    assert L.usp_solver_create(ctypes.byref(g), ctypes.byref(s), ctypes.c_void_p(1), 0, 0.0,
+                               None, ctypes.byref(h)) == _lib.ERR_INVALID_ARG
+    g = _grid((64, 64))
+    arr = (_lib.LSymbol * 2)(_lib.LSymbol(0.0, 0.3, 0.2, -0.5, 1, 16),
+                             _lib.LSymbol(0.0, 0.3, 0.2, -0.5))
+    al = (ctypes.c_double * 2)(0.0, 0.0)
+    assert L.usp_batch_create(ctypes.byref(g), 2, arr, ctypes.c_void_p(1), 0, al, None,
+                              ctypes.byref(h)) == _lib.ERR_INVALID_ARG
+    assert "single-problem" in _lib.last_error()
+    s = _lib.LSymbol(0.0, 0.3, 0.2, -0.5, 1, 16)
+    r = _lib.Result()
+    assert L.usp_solve_noalloc(ctypes.byref(g), ctypes.byref(s), ctypes.c_void_p(1), 0, 0.0,
+                               ctypes.c_void_p(1), ctypes.c_void_p(1), 1e-5, 10, None,
+                               ctypes.byref(r)) == _lib.ERR_INVALID_ARG
+
+
 def _batch_create(L, shape, syms, alphas=None, V=1):
     g = _grid(shape)
     count = len(syms)

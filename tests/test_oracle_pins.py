@@ -549,3 +549,29 @@ def test_history_is_relative_preconditioned_residual():
     assert ok and hist[-1] < tol and np.all(hist[:-1] >= tol)
     assert np.allclose(x.ravel(), xd, atol=1e-12 * np.abs(xd).max())
     assert uo.reference_norm(cf["y"], cf["V"], Lh) == pytest.approx(ref, rel=1e-12)
+
+
+# --------------------------------------------------- tabulated symbol ---
+
+@pytest.mark.parametrize("shape", [(12,), (6, 10), (4, 6, 8)])
+def test_table_symbol_equals_real_space_stencil(shape):
+    """The operators accept any tabulated symbol Lhat(p) (Sec. 2: L is any
+    translation-invariant operator, applied through its Fourier symbol).  With
+    the symbol of a periodic finite-difference operator, the oracle's L x is
+    that stencil applied in real space: pins the FFT-order frequency layout
+    (the drift term is odd in p, so a mirrored axis fails)."""
+    from symbol_tables import stencil_apply, stencil_symbol
+    dx, a, b, drift = 0.7, 0.3 - 0.2j, 0.1 + 0.4j, (0.9, -0.5, 0.3)
+    x = _rand(shape, 41)
+    T = stencil_symbol(shape, dx, a, b, drift).astype(np.complex128)
+    # the table is rounded to complex64: compare with the stencil of the same operator
+    got = uo.apply_L(x, T)
+    want = stencil_apply(x, dx, a, b, drift)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-6
+    # the FP64 table agrees to rounding
+    Texact = stencil_symbol(shape, dx, a, b, drift, dtype=np.complex128)
+    assert np.allclose(uo.apply_L(x, Texact), want, rtol=1e-12, atol=1e-12)
+    # the inverse of (L + I) through the same table solves the stencil system
+    u = uo.apply_L_plus_I_inverse(x, Texact)
+    assert np.allclose(stencil_apply(u, dx, a, b, drift) + u, x, rtol=1e-11, atol=1e-11)
+
