@@ -32,6 +32,7 @@ SOURCES = [
     "block_kernels.cu",
     "variant_api.cpp",
     "tc_kernels.cu",
+    "onchip_kernels.cu",
 ]
 
 

@@ -7,6 +7,7 @@
 namespace usp {
 
 // Iteration bookkeeping after ||Delta||^2 is known (Algorithm 1's test).
+// hist may be nullptr (a replica of the state that keeps no history).
 __device__ __forceinline__ void finalize_iteration(DevState* st, double* hist, double sumsq, int flags) {
   const double nrm = sqrt(sumsq);
   if (flags & F_REF) {
@@ -36,7 +37,7 @@ __device__ __forceinline__ void finalize_iteration(DevState* st, double* hist, d
   }
   const double r = ref > 0.0 ? nrm / ref : 0.0;
   const int it = st->it;
-  hist[it] = r;
+  if (hist) hist[it] = r;
   st->it = it + 1;
   st->last_r = r;
   if (it == st->phase_start) {

@@ -192,6 +192,29 @@ cudaError_t cols_tma_init();
 cudaError_t launch_cols_tma(int n, int cols, const CUtensorMap& map, const ColsTmaArgs& a, int grid,
                             cudaStream_t s);
 
+// Whole phases of the iteration for square 2-D grids n x n, n in {32, 64,
+// 128, 256}, resident in the shared memory of one cluster of n / 16 CTAs per
+// problem (onchip_kernels.cu).  One launch runs until every problem's state
+// says done; with F_REF it evaluates the reference norm only.
+struct OnchipArgs {
+  int flags;            // F_XZERO, F_REF, F_VREAL
+  const float2* x_in;   // iterate in (not read with F_XZERO)
+  float2* x_out;        // iterate out (may alias x_in; not written with F_REF)
+  const float2* y;
+  const void* V;        // complex64, or float32 with F_VREAL
+  const float2* tw;     // W_256^m table (device)
+  DevState* st;
+  double* hist;
+  float alpha;          // single problem (batches: bt.alpha)
+  Sym<float> sym;
+  Batch bt;
+};
+bool onchip_side(int n);
+// Clusters of the side-n kernel that fit on the device at once (0: the
+// kernel cannot be launched here).
+int onchip_clusters(int n);
+cudaError_t launch_onchip(int n, const OnchipArgs& a, int problems, cudaStream_t s);
+
 // Fused rows pass of the pencil schedule as a persistent, bulk-copy staged
 // kernel (tma_kernels.cu); row lengths 128 and 256.
 struct RowsTmaArgs {

@@ -134,6 +134,7 @@ struct usp_solver {
   int* bmask = nullptr;            // problems refined in the current phase, device
   int* bmask_host = nullptr;       // pinned mirror
   float2* table = nullptr;         // tabulated symbol Lhat(p) (USP_LSYM_TABLE), device
+  int onchip_clusters = 0;         // co-resident clusters of the on-chip schedule (0: unavailable)
   std::vector<double> alphas;      // per problem
   std::vector<std::vector<double>> histories;   // per problem, last solve
   int num_sms = 0;
@@ -412,6 +413,41 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
 
 // ---- fused two-pass schedule (grids nz x 256 x 256, fused3d_kernels.cu)
 
+// ---- on-chip schedule (square 2-D grids n x n, n in {32, 64, 128, 256},
+// onchip_kernels.cu): a whole phase of iterations per launch.
+
+static bool onchip_supported(const usp_solver* s) {
+  return s->ndim == 2 && s->n[0] == s->n[1] && onchip_side(s->n[0]) && s->onchip_clusters > 0;
+}
+// Automatic choice: on-chip wherever it applies (schedule 0); schedule 1
+// forces the pencil passes, schedule 3 the on-chip one.
+static bool use_onchip(const usp_solver* s) {
+  return onchip_supported(s) && (s->opt.schedule == 0 || s->opt.schedule == 3);
+}
+
+static OnchipArgs onchip_args(usp_solver* s, const float2* y, const float2* xin, float2* xout,
+                              int flags) {
+  OnchipArgs a{};
+  a.flags = flags | (s->vreal ? F_VREAL : 0);
+  a.x_in = xin;
+  a.x_out = xout;
+  a.y = y;
+  a.V = s->V;
+  a.tw = s->tw32;
+  a.st = s->st;
+  a.hist = s->hist;
+  a.alpha = (float)s->alpha;
+  a.sym = s->symf;
+  a.bt = batch_desc(s, 0);
+  return a;
+}
+
+static cudaError_t enqueue_onchip(usp_solver* s, const float2* y, const float2* xin, float2* xout,
+                                  int flags, cudaStream_t strm, bool count = true) {
+  if (count) g_launches.fetch_add(1);
+  return launch_onchip(s->n[0], onchip_args(s, y, xin, xout, flags), s->B, strm);
+}
+
 static bool fused_supported(const usp_solver* s) {
   return s->B == 1 && s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256 && s->plane_clusters > 0 &&
          s->maps_ok;
@@ -487,6 +523,8 @@ static std::vector<PassLaunch> prologue_passes(usp_solver* s, const float2* y, c
 static cudaError_t enqueue_iteration(usp_solver* s, const float2* y, const float2* xin,
                                      float2* xout, int flags, cudaStream_t strm,
                                      bool count = true, bool first = false) {
+  if (use_onchip(s))  // the reference pass (F_REF) or a whole phase
+    return enqueue_onchip(s, y, xin, xout, flags, strm, count);
   if (first) {
     for (auto& p : prologue_passes(s, y, xin, flags)) {
       cudaError_t e = p.go(strm);
@@ -773,6 +811,7 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   build_maps(s);
   if (count == 1 && s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256)
     s->plane_clusters = plane_max_active_clusters();
+  if (s->ndim == 2 && s->n[0] == s->n[1] && onchip_side(s->n[0])) s->onchip_clusters = onchip_clusters(s->n[0]);
   *out = s;
   return USP_OK;
 #undef CREATE_TRY
@@ -794,10 +833,12 @@ extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* o
   if (!s || !opt) return fail(USP_ERR_INVALID_ARG, "NULL argument");
   if (opt->cols_tile != 0 && opt->cols_tile != 8 && opt->cols_tile != 16 && opt->cols_tile != 32)
     return fail(USP_ERR_INVALID_ARG, "cols_tile must be 0, 8, 16 or 32");
-  if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 2)
+  if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 3)
     return fail(USP_ERR_INVALID_ARG, "invalid option value");
   if (opt->schedule == 2 && !fused_supported(s))
     return fail(USP_ERR_UNSUPPORTED_SIZE, "the fused schedule needs a 3-D grid nz x 256 x 256");
+  if (opt->schedule == 3 && !onchip_supported(s))
+    return fail(USP_ERR_UNSUPPORTED_SIZE, "the on-chip schedule needs a 2-D grid n x n, n in {32, 64, 128, 256}");
   free_graphs(s);  // captured graphs follow the old schedule
   s->opt = *opt;
   return USP_OK;
@@ -864,6 +905,17 @@ static usp_status write_state(usp_solver* s) {
 
 // Run iterations on (y, x) until every problem's device state says done.
 static usp_status run_phase(usp_solver* s, const float2* y, float2* x, bool zero_start) {
+  if (use_onchip(s)) {
+    // one launch runs the phase to the end
+    cudaError_t e = enqueue_onchip(s, y, x, x, zero_start ? F_XZERO : 0, s->stream);
+    if (e != cudaSuccess) return fail(USP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    usp_status st = read_state(s);
+    if (st != USP_OK) return st;
+    for (int p = 0; p < s->B; ++p)
+      if (!s->st_host[p].done)
+        return fail(USP_ERR_CUDA, "on-chip phase ended with a running problem (%d)", p);
+    return USP_OK;
+  }
   const int chunk = s->opt.chunk > 0 ? s->opt.chunk : 8;
   // the first iteration is launched directly (it may start from x = 0)
   {
@@ -1298,11 +1350,36 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
   for (int p = 0; p < s->B; ++p) {
     DevState& h = s->st_host[p];
     std::memset(&h, 0, sizeof h);
-    h.it_limit = iters + 1;
+    h.it_limit = use_onchip(s) ? iters : iters + 1;  // on-chip: one launch runs them all
     h.ref = 1.0;   // fixed denominator: nothing stops the timed iterations
     h.tol = 0.0;
   }
   if ((st = write_state(s)) != USP_OK) return st;
+  if (use_onchip(s)) {
+    // one launch of `iters` iterations; its mean per iteration
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    cudaError_t e = cudaEventRecord(e0, s->stream);
+    if (e == cudaSuccess) e = enqueue_onchip(s, (const float2*)y, (const float2*)x, (float2*)x, 0, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(USP_ERR_CUDA, "timing launch: %s", cudaGetErrorString(e));
+    if (capacity > 0) {
+      std::memset(out[0].name, 0, sizeof out[0].name);
+      std::strncpy(out[0].name, "onchip_iteration", sizeof out[0].name - 1);
+      out[0].launches = 1;
+      out[0].ms = ms / iters;
+      out[0].bytes = 0.0;  // the fields stay on chip between iterations
+    }
+    *n_out = 1;
+    if (cur != s->device) cudaSetDevice(cur);
+    return USP_OK;
+  }
   for (auto& p : prologue_passes(s, (const float2*)y, (const float2*)x, 0)) {
     cudaError_t e = p.go(s->stream);
     if (e != cudaSuccess) return fail(USP_ERR_CUDA, "prologue: %s", cudaGetErrorString(e));
@@ -1385,6 +1462,11 @@ extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_
         o.cols_tile = ct;
         cands.push_back(o);
       }
+  if (onchip_supported(s)) {
+    usp_options o = s->opt;
+    o.schedule = 3;
+    cands.push_back(o);
+  }
   const usp_options keep = s->opt;
   double best_ms = 1e300;
   for (const usp_options& o : cands) {

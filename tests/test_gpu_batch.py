@@ -55,9 +55,9 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def _check_trajectories(torch, shape, probs, n_iter, vreal=False):
+def _check_trajectories(torch, shape, probs, n_iter, vreal=False, schedule=0):
     cfs, V, y = _prep(probs, vreal)
-    with _batch(torch, shape, cfs, V, plain=True) as s:
+    with _batch(torch, shape, cfs, V, plain=True, schedule=schedule) as s:
         x, res = s.solve(torch.from_numpy(y).to("cuda:0"), tol=0.0, maxit=n_iter)
         hists = [s.history(j) for j in range(len(probs))]
         xg = x.cpu().numpy().astype(np.complex128)
@@ -75,18 +75,21 @@ def _check_trajectories(torch, shape, probs, n_iter, vreal=False):
                                               rel=1e-5)
 
 
-@pytest.mark.parametrize("shape, count", [
-    ((64, 64), 5),          # plain line passes
-    ((128, 128), 3),        # staged line pass, 2 tiles per problem
-    ((16, 64, 64), 2),
-    ((8, 128, 128), 2),     # staged line and column passes
-    ((96, 96), 3),          # radix-3 lines
-    ((512, 64), 2),         # radix-2 outer stage on the strided axis
+@pytest.mark.parametrize("shape, count, schedule", [
+    ((64, 64), 5, 1),          # plain line passes
+    ((128, 128), 3, 1),        # staged line pass, 2 tiles per problem
+    ((16, 64, 64), 2, 0),
+    ((8, 128, 128), 2, 0),     # staged line and column passes
+    ((96, 96), 3, 0),          # radix-3 lines
+    ((512, 64), 2, 0),         # radix-2 outer stage on the strided axis
+    ((64, 64), 5, 0),          # on-chip: one cluster per problem
+    ((128, 128), 3, 0),
+    ((256, 256), 2, 0),
 ])
-def test_batch_trajectories_match_oracle(torch_cuda, shape, count):
+def test_batch_trajectories_match_oracle(torch_cuda, shape, count, schedule):
     probs = [inputs.random_helmholtz(shape, 100 + j, sigma_px=2.0 + j,
                                      amplitude=0.1 + 0.1 * j) for j in range(count)]
-    _check_trajectories(torch_cuda, shape, probs, 30)
+    _check_trajectories(torch_cuda, shape, probs, 30, schedule=schedule)
 
 
 def test_batch_full_size_problems_256(torch_cuda):
@@ -311,7 +314,8 @@ def test_autotune_choice_is_cached_per_shape(torch_cuda):
     with _batch(torch, shape, cfs, V) as s:
         t2 = s.autotune(yd, iters=2)
     assert t1 == t2
-    assert t1["schedule"] == 1 and 4 <= t1["chunk"] <= 64
+    # square 128^2: the on-chip schedule (several times faster than the passes)
+    assert t1["schedule"] == 3 and 4 <= t1["chunk"] <= 64
     for j, cf in enumerate(cfs):
         V64, y64 = V[j].astype(np.complex128), y[j].astype(np.complex128)
         d = uo.residual_delta(x[j].cpu().numpy().astype(np.complex128), y64, V64, _lh(shape, cf))
