@@ -21,6 +21,7 @@ Multi-GPU runs are independent replicas (the solve does not shard).
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -177,6 +178,36 @@ def measured_hbm_peak():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+# FP32 lanes per SM (Blackwell): the ALU peak of the on-chip schedule, whose
+# fields stay in shared memory between iterations (no HBM traffic to bound it).
+FP32_LANES_PER_SM = 128
+NOMINAL_SM_MHZ = 2070.0
+
+
+def onchip_flop_per_point(n):
+    """Algorithmic flops per grid point of one on-chip iteration on an n x n
+    grid: forward and inverse 2-D FFT at 5 log2(N) each (N = n^2), plus 40
+    pointwise ((1 - V) x + y: 8; multiplier 1/(N (Lhat + 1)): 14 with the
+    complex product; Delta = (1 - V)(u - x): 8; update 4; |Delta|^2: 4;
+    rounded up)."""
+    return 2 * 5 * math.log2(n * n) + 40
+
+
+def onchip_roofline(passes, problems, n, torch, dev, sm_mhz=None):
+    """ALU roofline of an on-chip iteration (one kernel per phase; its mean
+    per iteration from usp_time_passes)."""
+    ms = sum(p["ms"] for p in passes)
+    flop = onchip_flop_per_point(n) * n * n * problems
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz or NOMINAL_SM_MHZ
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flop / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "onchip_iteration", "iteration_ms": ms,
+            "flop_per_iteration": flop, "achieved_tflops": achieved,
+            "peak_tflops": peak, "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz"
+            % (sms, FP32_LANES_PER_SM, mhz), "frac": achieved / peak}
 
 
 # Sources of the pencil-schedule kernels whose ncu traffic is recorded.
@@ -374,6 +405,7 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
                         "iter_per_s": r["iterations"] / dt,
                         "s_to_min_residual": dt * (int(h.argmin()) + 1) / r["iterations"]}
     out["library_comparator"] = cufft_leg(torch, dev, cf, V, y, shape)
+    out["helmholtz2d_128"] = helmholtz2d_leg(args, torch, dev)
     if args.batch > 0:
         out["batched"] = batched_leg(args, torch, dev)
     if args.mixed > 0:
@@ -545,8 +577,13 @@ def mixed_batch_leg(args, torch, dev):
             sv.solve(yg[n], x=xt, tol=0.0, maxit=3)
             ps = sv.time_passes(yg[n], xt, iters=10)
         ms = sum(p["ms"] for p in ps)
-        per_side[str(n)] = {"iteration_ms": round(ms, 5),
-                            "frac": round(sum(p["bytes"] for p in ps) / (ms * 1e-3) / 1e9 / peak, 3)}
+        if ps[0]["name"] == "onchip_iteration":
+            rf = onchip_roofline(ps, len(groups[n]), n, torch, dev)
+            per_side[str(n)] = {"iteration_ms": round(ms, 5), "schedule": "on-chip",
+                                "bound": "alu", "frac": round(rf["frac"], 3)}
+        else:
+            per_side[str(n)] = {"iteration_ms": round(ms, 5), "schedule": "pencil", "bound": "hbm",
+                                "frac": round(sum(p["bytes"] for p in ps) / (ms * 1e-3) / 1e9 / peak, 3)}
     out = {"problems": args.mixed, "tol": args.tol, "per_side_iteration": per_side,
            "sides": {str(n): len(groups[n]) for n in sides},
            "points": int(sum(pts[n] * len(groups[n]) for n in sides)),
@@ -601,6 +638,39 @@ def cufft_leg(torch, dev, cf, V, y, shape, iters=20):
             "iter_per_s": 1e3 / ms, "ms_per_iter": ms}
 
 
+def helmholtz2d_leg(args, torch, dev):
+    """One 2-D 128 x 128 Helmholtz problem (sigma 4 px, amplitude 0.3, ABL 16
+    px, centre point source) to the bench tolerance with refinement: the
+    on-chip schedule (automatic for this grid) against the pencil passes."""
+    from paper_2207_14222_gb300 import canon, inputs
+    from paper_2207_14222_gb300.solver import Solver
+    n = 128
+    cf = canon.canonical(inputs.helmholtz_2d(n, seed=0))
+    V = torch.from_numpy(np.asarray(cf["V"], np.complex64)).to(dev)
+    y = torch.from_numpy(np.asarray(cf["y"], np.complex64)).to(dev)
+    out = {"grid": [n, n], "tol": args.tol, "step": "solve to tol (solver created once)"}
+    for name, sched in (("onchip", 3), ("pencil", 1)):
+        with Solver((n, n), cf["a"], cf["b"], V, dx=cf["dx"], schedule=sched) as s:
+            x = torch.empty_like(y)
+            for _ in range(3):
+                s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
+            torch.cuda.synchronize()
+            reps = 20
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                _, r = s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+            ps = s.time_passes(y, x, iters=200)
+        d = {"s_to_residual": dt, "iterations": r["iterations"], "refinements": r["refinements"],
+             "converged": bool(r["converged"]), "us_per_iteration": 1e3 * sum(p["ms"] for p in ps)}
+        if sched == 3:
+            d["roofline"] = onchip_roofline(ps, 1, n, torch, dev)
+        out[name] = d
+    out["speedup"] = out["pencil"]["s_to_residual"] / out["onchip"]["s_to_residual"]
+    return out
+
+
 def batched_leg(args, torch, dev):
     """Many small 2-D problems (the 128x128 medium distribution, one seed
     each): solved together by one batch solver vs one solver per problem,
@@ -637,11 +707,14 @@ def batched_leg(args, torch, dev):
         passes = s.time_passes(y, xt, iters=20)
     peak, _ = measured_hbm_peak()
     it_ms = sum(p["ms"] for p in passes)
-    out["roofline"] = {"iteration_ms": it_ms,
-                       "iteration_frac": sum(p["bytes"] for p in passes) / (it_ms * 1e-3) / 1e9 / peak,
-                       "passes": [{"name": p["name"], "ms": round(p["ms"], 5),
-                                   "GBps": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)}
-                                  for p in passes]}
+    if passes[0]["name"] == "onchip_iteration":
+        out["roofline"] = onchip_roofline(passes, B, n, torch, dev)
+    else:
+        out["roofline"] = {"iteration_ms": it_ms,
+                           "iteration_frac": sum(p["bytes"] for p in passes) / (it_ms * 1e-3) / 1e9 / peak,
+                           "passes": [{"name": p["name"], "ms": round(p["ms"], 5),
+                                       "GBps": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)}
+                                      for p in passes]}
     for name, fn in (("batched", batched), ("one_by_one", one_by_one)):
         fn()  # warm-up
         torch.cuda.synchronize()

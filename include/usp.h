@@ -111,9 +111,13 @@ typedef struct {
    *    has exactly the same Delta (A + B = L + I, Sec. 2.1); x = x + z.
    * 1: plain -- Algorithm 1 exactly: stop at tol or maxit.                 */
   int32_t plain;
-  /* 0: automatic; 1: pencil schedule (one FFT axis per pass);
-   * 2: fused 3-D schedule (two passes per iteration; 3-D grids whose three
-   *    axes are all 256).                                                  */
+  /* 0: automatic (on-chip where it applies, else pencil);
+   * 1: pencil schedule (one FFT axis per pass);
+   * 2: fused 3-D schedule (two passes per iteration; 3-D grids nz x 256 x
+   *    256, single problem);
+   * 3: on-chip schedule (square 2-D grids n x n, n in {32, 64, 128, 256}):
+   *    each problem's fields stay in the shared memory of one thread-block
+   *    cluster and one launch runs a whole phase of iterations.            */
   int32_t schedule;
   /* iterations per CUDA-graph launch between convergence polls; 0: auto   */
   int32_t chunk;
@@ -129,6 +133,9 @@ typedef struct {
    *    tensor cores (tcgen05, TF32 split into three products for FP32-level
    *    accuracy; single problems, pencil schedule); 0: CUDA cores           */
   int32_t tc_dft;
+  /* rows (and k-space columns) per CTA of the on-chip schedule: 16, or 8
+   * (n <= 128; twice the CTAs per problem), or 0 for the library's choice */
+  int32_t onchip_rows;
 } usp_options;
 
 typedef struct usp_solver usp_solver;

@@ -210,10 +210,12 @@ struct OnchipArgs {
   Batch bt;
 };
 bool onchip_side(int n);
-// Clusters of the side-n kernel that fit on the device at once (0: the
-// kernel cannot be launched here).
-int onchip_clusters(int n);
-cudaError_t launch_onchip(int n, const OnchipArgs& a, int problems, cudaStream_t s);
+// rows: rows (and k-space columns) per CTA, 16 or 8 (8 for n <= 128).
+bool onchip_rows_ok(int n, int rows);
+// Clusters of the kernel for (n, rows) that fit on the device at once (0:
+// it cannot be launched here).
+int onchip_clusters(int n, int rows);
+cudaError_t launch_onchip(int n, int rows, const OnchipArgs& a, int problems, cudaStream_t s);
 
 // Fused rows pass of the pencil schedule as a persistent, bulk-copy staged
 // kernel (tma_kernels.cu); row lengths 128 and 256.

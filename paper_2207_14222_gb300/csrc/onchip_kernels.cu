@@ -33,10 +33,10 @@
 namespace usp {
 namespace {
 
-template <int N>
+template <int N, int RR>
 struct OnchipCfg {
-  static constexpr int C = N / 16;           // CTAs per cluster
-  static constexpr int R = 16;               // rows (and k-space columns) per CTA
+  static constexpr int R = RR;               // rows (and k-space columns) per CTA
+  static constexpr int C = N / R;            // CTAs per cluster
   static constexpr int G = Split<N>::G;      // threads per line
   static constexpr int NV = Split<N>::N1;    // values per thread
   static constexpr int T = R * G;            // threads per CTA
@@ -46,6 +46,8 @@ struct OnchipCfg {
   static constexpr size_t SMEM = sizeof(float2) * (5 * (size_t)FIELD + N) + sizeof(double) * (C + T / 32);
   static_assert(Split<N>::N1 * Split<N>::N2 == N, "length");
   static_assert(T % 32 == 0, "whole warps");
+  static_assert(C >= 2 && C <= 16, "cluster size");
+  static_assert(G <= 32 && 32 % G == 0, "the threads of a line share a warp");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -85,6 +87,8 @@ __device__ __forceinline__ float2 linv_factor(float lr, float li, float inv_n) {
   return make_float2(dr * sc, -li * sc);
 }
 
+// A line of N values held by its G threads (one warp holds whole lines, so
+// the exchange needs only warp synchronisation).
 template <int N>
 __device__ __forceinline__ void fft_line(float2* v, float2* ex, const float2* tw, int g, bool inv) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
@@ -92,7 +96,7 @@ __device__ __forceinline__ void fft_line(float2* v, float2* ex, const float2* tw
   else stage1<N, false>(v, g, tw);
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) ex[k1 * N2 + (g ^ (k1 & (N2 - 1)))] = v[k1];
-  __syncthreads();
+  __syncwarp();
   float2 w[N1];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
@@ -100,16 +104,16 @@ __device__ __forceinline__ void fft_line(float2* v, float2* ex, const float2* tw
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[k1 * N2 + (n2 ^ (k1 & (N2 - 1)))];
   }
-  __syncthreads();
+  __syncwarp();
   if (inv) stage2<N, true>(w);
   else stage2<N, false>(w);
 #pragma unroll
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
-template <int N>
-__global__ void __launch_bounds__(OnchipCfg<N>::T, 1) k_onchip(OnchipArgs a) {
-  typedef OnchipCfg<N> K;
+template <int N, int RR>
+__global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a) {
+  typedef OnchipCfg<N, RR> K;
   constexpr int C = K::C, R = K::R, G = K::G, NV = K::NV, T = K::T, P = K::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(OnchipCfg<N>::T, 1) k_onchip(OnchipArgs a) {
     // ---- B: FFT along y, multiply, inverse FFT along y, values to row owners
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = cb[kk * P + in_index<N>(g2, q)];
-    __syncthreads();
+    __syncwarp();  // a column's threads share a warp
     fft_line<N>(v, cb + kk * P, tw, g2, false);
     if (sy.table) {
 #pragma unroll
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(OnchipCfg<N>::T, 1) k_onchip(OnchipArgs a) {
     // ---- C: inverse FFT along x, Delta, update, |Delta|^2 to every CTA
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = rb[j * P + in_index<N>(g, q)];
-    __syncthreads();
+    __syncwarp();  // a row's threads share a warp
     fft_line<N>(v, rb + j * P, tw, g, true);
     float ss = 0.f;
 #pragma unroll
@@ -274,9 +278,9 @@ __global__ void __launch_bounds__(OnchipCfg<N>::T, 1) k_onchip(OnchipArgs a) {
   }
 }
 
-template <int N>
+template <int N, int RR>
 cudaError_t launch_n(const OnchipArgs& a, int problems, cudaStream_t s) {
-  typedef OnchipCfg<N> K;
+  typedef OnchipCfg<N, RR> K;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(K::C * problems), 1, 1);
   cfg.blockDim = dim3(K::T, 1, 1);
@@ -289,16 +293,16 @@ cudaError_t launch_n(const OnchipArgs& a, int problems, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_onchip<N>, a);
+  return cudaLaunchKernelEx(&cfg, k_onchip<N, RR>, a);
 }
 
-template <int N>
+template <int N, int RR>
 int prepare_n() {
-  typedef OnchipCfg<N> K;
-  if (cudaFuncSetAttribute(k_onchip<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM) !=
+  typedef OnchipCfg<N, RR> K;
+  if (cudaFuncSetAttribute(k_onchip<N, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM) !=
       cudaSuccess)
     return 0;
-  if (K::C > 8 && cudaFuncSetAttribute(k_onchip<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+  if (K::C > 8 && cudaFuncSetAttribute(k_onchip<N, RR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                       cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
@@ -313,7 +317,7 @@ int prepare_n() {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_onchip<N>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_onchip<N, RR>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -324,24 +328,45 @@ int prepare_n() {
 
 bool onchip_side(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
-int onchip_clusters(int n) {
-  switch (n) {
-    case 32: return prepare_n<32>();
-    case 64: return prepare_n<64>();
-    case 128: return prepare_n<128>();
-    case 256: return prepare_n<256>();
-    default: return 0;
+// rows: rows per CTA, 16 or 8 (8 only for n <= 128: at most 16 CTAs).
+bool onchip_rows_ok(int n, int rows) { return onchip_side(n) && (rows == 16 || (rows == 8 && n <= 128)); }
+
+int onchip_clusters(int n, int rows) {
+  if (!onchip_rows_ok(n, rows)) return 0;
+  if (rows == 8) {
+    switch (n) {
+      case 32: return prepare_n<32, 8>();
+      case 64: return prepare_n<64, 8>();
+      case 128: return prepare_n<128, 8>();
+    }
+    return 0;
   }
+  switch (n) {
+    case 32: return prepare_n<32, 16>();
+    case 64: return prepare_n<64, 16>();
+    case 128: return prepare_n<128, 16>();
+    case 256: return prepare_n<256, 16>();
+  }
+  return 0;
 }
 
-cudaError_t launch_onchip(int n, const OnchipArgs& a, int problems, cudaStream_t s) {
-  switch (n) {
-    case 32: return launch_n<32>(a, problems, s);
-    case 64: return launch_n<64>(a, problems, s);
-    case 128: return launch_n<128>(a, problems, s);
-    case 256: return launch_n<256>(a, problems, s);
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_onchip(int n, int rows, const OnchipArgs& a, int problems, cudaStream_t s) {
+  if (!onchip_rows_ok(n, rows)) return cudaErrorInvalidValue;
+  if (rows == 8) {
+    switch (n) {
+      case 32: return launch_n<32, 8>(a, problems, s);
+      case 64: return launch_n<64, 8>(a, problems, s);
+      case 128: return launch_n<128, 8>(a, problems, s);
+    }
+    return cudaErrorInvalidValue;
   }
+  switch (n) {
+    case 32: return launch_n<32, 16>(a, problems, s);
+    case 64: return launch_n<64, 16>(a, problems, s);
+    case 128: return launch_n<128, 16>(a, problems, s);
+    case 256: return launch_n<256, 16>(a, problems, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace usp

@@ -134,7 +134,7 @@ struct usp_solver {
   int* bmask = nullptr;            // problems refined in the current phase, device
   int* bmask_host = nullptr;       // pinned mirror
   float2* table = nullptr;         // tabulated symbol Lhat(p) (USP_LSYM_TABLE), device
-  int onchip_clusters = 0;         // co-resident clusters of the on-chip schedule (0: unavailable)
+  int onchip_clusters[2] = {0, 0}; // co-resident clusters of the on-chip kernels with 8 / 16 rows per CTA
   std::vector<double> alphas;      // per problem
   std::vector<std::vector<double>> histories;   // per problem, last solve
   int num_sms = 0;
@@ -416,13 +416,27 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
 // ---- on-chip schedule (square 2-D grids n x n, n in {32, 64, 128, 256},
 // onchip_kernels.cu): a whole phase of iterations per launch.
 
-static bool onchip_supported(const usp_solver* s) {
-  return s->ndim == 2 && s->n[0] == s->n[1] && onchip_side(s->n[0]) && s->onchip_clusters > 0;
+// Rows per CTA: the option, else 16.
+static int onchip_rows_of(const usp_solver* s, const usp_options& o) {
+  return o.onchip_rows > 0 ? o.onchip_rows : 16;
 }
-// Automatic choice: on-chip wherever it applies (schedule 0); schedule 1
-// forces the pencil passes, schedule 3 the on-chip one.
+static bool onchip_available(const usp_solver* s, int rows) {
+  return s->ndim == 2 && s->n[0] == s->n[1] && onchip_rows_ok(s->n[0], rows) &&
+         s->onchip_clusters[rows == 8 ? 0 : 1] > 0;
+}
+static bool onchip_supported(const usp_solver* s) { return onchip_available(s, onchip_rows_of(s, s->opt)); }
+// Schedule 3 forces the on-chip kernels, schedule 1 the pencil passes.  The
+// automatic choice (0) takes on-chip where it applies unless the problems'
+// clusters do not all fit on the device at once and each holds 16 SMs' worth
+// of shared memory (n = 256): there the passes keep more SMs busy (measured:
+// 64 problems of 256^2, 75 us per pencil iteration against 108 us on chip;
+// 64 of 128^2, 35 us against 17 us).
 static bool use_onchip(const usp_solver* s) {
-  return onchip_supported(s) && (s->opt.schedule == 0 || s->opt.schedule == 3);
+  if (!onchip_supported(s)) return false;
+  if (s->opt.schedule == 3) return true;
+  if (s->opt.schedule != 0) return false;
+  const int rows = onchip_rows_of(s, s->opt);
+  return s->n[0] <= 128 || s->B <= s->onchip_clusters[rows == 8 ? 0 : 1];
 }
 
 static OnchipArgs onchip_args(usp_solver* s, const float2* y, const float2* xin, float2* xout,
@@ -445,7 +459,7 @@ static OnchipArgs onchip_args(usp_solver* s, const float2* y, const float2* xin,
 static cudaError_t enqueue_onchip(usp_solver* s, const float2* y, const float2* xin, float2* xout,
                                   int flags, cudaStream_t strm, bool count = true) {
   if (count) g_launches.fetch_add(1);
-  return launch_onchip(s->n[0], onchip_args(s, y, xin, xout, flags), s->B, strm);
+  return launch_onchip(s->n[0], onchip_rows_of(s, s->opt), onchip_args(s, y, xin, xout, flags), s->B, strm);
 }
 
 static bool fused_supported(const usp_solver* s) {
@@ -811,7 +825,10 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   build_maps(s);
   if (count == 1 && s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256)
     s->plane_clusters = plane_max_active_clusters();
-  if (s->ndim == 2 && s->n[0] == s->n[1] && onchip_side(s->n[0])) s->onchip_clusters = onchip_clusters(s->n[0]);
+  if (s->ndim == 2 && s->n[0] == s->n[1] && onchip_side(s->n[0])) {
+    s->onchip_clusters[0] = onchip_clusters(s->n[0], 8);
+    s->onchip_clusters[1] = onchip_clusters(s->n[0], 16);
+  }
   *out = s;
   return USP_OK;
 #undef CREATE_TRY
@@ -837,8 +854,11 @@ extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* o
     return fail(USP_ERR_INVALID_ARG, "invalid option value");
   if (opt->schedule == 2 && !fused_supported(s))
     return fail(USP_ERR_UNSUPPORTED_SIZE, "the fused schedule needs a 3-D grid nz x 256 x 256");
-  if (opt->schedule == 3 && !onchip_supported(s))
-    return fail(USP_ERR_UNSUPPORTED_SIZE, "the on-chip schedule needs a 2-D grid n x n, n in {32, 64, 128, 256}");
+  if (opt->onchip_rows != 0 && opt->onchip_rows != 8 && opt->onchip_rows != 16)
+    return fail(USP_ERR_INVALID_ARG, "onchip_rows must be 0, 8 or 16");
+  if (opt->schedule == 3 && !onchip_available(s, onchip_rows_of(s, *opt)))
+    return fail(USP_ERR_UNSUPPORTED_SIZE,
+                "the on-chip schedule needs a 2-D grid n x n, n in {32, 64, 128, 256} (8 rows per CTA: n <= 128)");
   free_graphs(s);  // captured graphs follow the old schedule
   s->opt = *opt;
   return USP_OK;
@@ -1462,11 +1482,13 @@ extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_
         o.cols_tile = ct;
         cands.push_back(o);
       }
-  if (onchip_supported(s)) {
-    usp_options o = s->opt;
-    o.schedule = 3;
-    cands.push_back(o);
-  }
+  for (int rows = 8; rows <= 16; rows += 8)
+    if (onchip_available(s, rows)) {
+      usp_options o = s->opt;
+      o.schedule = 3;
+      o.onchip_rows = rows;
+      cands.push_back(o);
+    }
   const usp_options keep = s->opt;
   double best_ms = 1e300;
   for (const usp_options& o : cands) {

@@ -39,7 +39,7 @@ class Solver:
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
                  schedule=0, chunk=0, max_refinements=0, no_tma=False, cols_tile=0,
-                 tc_dft=False, lhat_table=None):
+                 tc_dft=False, lhat_table=None, onchip_rows=0):
         """Lhat(p) = a |p|^2 + b, or, with `lhat_table` (a complex64 CUDA tensor of the
         grid's shape, k-space in FFT order), the tabulated symbol; a and b are then
         ignored."""
@@ -79,12 +79,12 @@ class Solver:
         self._h = h
         self.set_options(plain=plain, schedule=schedule, chunk=chunk,
                          max_refinements=max_refinements, no_tma=no_tma, cols_tile=cols_tile,
-                         tc_dft=tc_dft)
+                         tc_dft=tc_dft, onchip_rows=onchip_rows)
 
     def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False,
-                    cols_tile=0, tc_dft=False):
+                    cols_tile=0, tc_dft=False, onchip_rows=0):
         o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements),
-                    int(bool(no_tma)), int(cols_tile), int(bool(tc_dft)))
+                    int(bool(no_tma)), int(cols_tile), int(bool(tc_dft)), int(onchip_rows))
         check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
 
     @property
@@ -209,7 +209,7 @@ class BatchSolver(Solver):
     """
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
-                 schedule=0, chunk=0, max_refinements=0, no_tma=False):
+                 schedule=0, chunk=0, max_refinements=0, no_tma=False, onchip_rows=0):
         import torch
         L = _lib.lib()
         if not V.is_cuda:
@@ -248,7 +248,7 @@ class BatchSolver(Solver):
                                      ctypes.c_void_p(stream), ctypes.byref(h)))
         self._h = h
         self.set_options(plain=plain, schedule=schedule, chunk=chunk,
-                         max_refinements=max_refinements, no_tma=no_tma)
+                         max_refinements=max_refinements, no_tma=no_tma, onchip_rows=onchip_rows)
 
     def solve(self, y, x=None, tol=1e-6, maxit=10000, ref_norms=None, use_x0=False,
               allow_failed=True):
