@@ -5,30 +5,37 @@
 // The pencil schedule streams the field through HBM two or three times per
 // iteration; at n <= 256 a field is at most 512 KiB, so those passes are
 // latency-bound launches of a few dozen blocks.  Here one cluster of C CTAs
-// holds the problem: CTA c owns rows [c R, c R + R) of x, V and y (R = n / C
-// = 16) and, in k-space, columns [c R, c R + R).  One iteration is
+// holds the problem: CTA c owns rows [c R, c R + R) of x, V and y and, in
+// k-space, columns [c R, c R + R).  One iteration is
 //   A  t = (1 - V) x + y on the own rows, FFT along x, each k-space value
 //      stored into the shared memory of the CTA that owns its column;
 //   B  FFT along y of the own columns, the multiplier 1/(N (Lhat + 1)),
 //      inverse FFT along y, each value stored back to the owner of its row;
 //   C  inverse FFT along x, Delta = (1 - V)(u - x), x += alpha Delta, and
 //      the CTA's sum of |Delta|^2 stored into every CTA of the cluster.
-// Two cluster barriers per iteration: after A (which also publishes the
-// previous iteration's norm sums) and after B.  Every CTA adds the C sums in
-// the same order and runs the same convergence test (Algorithm 1's) on its
-// own copy of the device state, so all CTAs leave the loop together; rank 0
-// writes the history and the state.  The next iteration's step A runs before
-// the test of the current one is read (its result is dropped if the test
-// stops the phase), which saves the third barrier.
+// The stores between CTAs are asynchronous (st.async) and count their bytes
+// on an mbarrier of the receiving CTA, so a CTA waits only for the data it
+// needs, not for the whole cluster.  No buffer is overwritten early: a CTA
+// sends the next round into a buffer only after it has received data that
+// its owner sends after reading that buffer, and every CTA arms the next
+// phase of its mbarriers right after a wait completes, before it sends the
+// data that lets anyone produce for that phase.  Every CTA adds the C sums
+// in the same order and runs the same convergence test (Algorithm 1's) on
+// its own copy of the device state, so all CTAs leave the loop together;
+// rank 0 writes the history and the state.  The next iteration's step A runs
+// before the test of the current one is read (its result is dropped if the
+// test stops the phase).
 //
 // One launch runs a whole phase (until the state says done), one cluster per
-// problem of a batch.
+// problem of a batch.  Every wait is bounded; one that gives up records
+// ST_TIMEOUT and the CTAs meet at a final cluster barrier before they exit.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "fft_core.cuh"
 #include "iteration_state.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace usp {
 namespace {
@@ -50,9 +57,6 @@ struct OnchipCfg {
   static_assert(G <= 32 && 32 % G == 0, "the threads of a line share a warp");
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -64,16 +68,45 @@ __device__ __forceinline__ uint32_t map_rank(const void* p, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+// Asynchronous store into the shared memory of a CTA of the cluster; its
+// bytes complete on the mbarrier `mbar` (same CTA, shared::cluster address).
+__device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(mbar)
+               : "memory");
 }
-__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+               "l"(__double_as_longlong(v)), "r"(mbar)
+               : "memory");
 }
-// All threads of all CTAs of the cluster; stores before it (local or remote)
-// are visible after it.
+// Bounded wait for a phase of a local mbarrier whose bytes come from other
+// CTAs of the cluster (acquire at cluster scope makes their stores visible).
+__device__ __forceinline__ bool wait_cluster(uint64_t* b, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// All threads of all CTAs of the cluster.
 __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Position of element e of line l in a line buffer (stride P): an XOR of
+// bits 1-3 of e that puts the values one warp stores into one line each
+// (step A into columns, step B into rows) and the values it loads along its
+// lines on distinct banks.
+template <int G>
+__device__ __forceinline__ int swz(int l, int e) {
+  return e ^ (((l >> 1) * (16 / G)) & 7);
 }
 
 __device__ __forceinline__ float axis_p2(const Sym<float>& s, int ax, int k) {
@@ -115,6 +148,8 @@ template <int N, int RR>
 __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a) {
   typedef OnchipCfg<N, RR> K;
   constexpr int C = K::C, R = K::R, G = K::G, NV = K::NV, T = K::T, P = K::P;
+  constexpr uint32_t LINE_BYTES = (uint32_t)(R * N * sizeof(float2));   // one round into rb or cb
+  constexpr uint32_t SLOT_BYTES = (uint32_t)(C * sizeof(double));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* xs = reinterpret_cast<float2*>(smem_raw);
   float2* vs = xs + K::FIELD;
@@ -125,7 +160,9 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   double* slots = reinterpret_cast<double*>(tw + N);   // |Delta|^2 of each CTA
   double* red = slots + C;
   __shared__ DevState S;
-  __shared__ uint32_t r_rb[C], r_cb[C], r_sl[C];
+  __shared__ __align__(8) uint64_t mb[3];   // cb, rb, slots full
+  __shared__ uint32_t r_rb[C], r_cb[C], r_sl[C], m_rb[C], m_cb[C], m_sl[C];
+  __shared__ int fail;
 
   const int tid = threadIdx.x;
   const uint32_t c = cluster_rank();
@@ -139,12 +176,26 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   const bool ref_pass = (a.flags & F_REF) != 0;
   const bool xzero = (a.flags & F_XZERO) != 0;
 
-  if (tid == 0) S = *gst;
+  if (tid == 0) {
+    S = *gst;
+    fail = 0;
+    if (!S.done) {
+      for (int b = 0; b < 3; ++b) mbar_init(&mb[b], 1);
+      fence_mbar_init();
+      // first phase of each barrier armed before any CTA can send
+      mbar_arrive_expect_tx(&mb[0], LINE_BYTES);
+      mbar_arrive_expect_tx(&mb[1], LINE_BYTES);
+      mbar_arrive_expect_tx(&mb[2], SLOT_BYTES);
+    }
+  }
   for (int m = tid; m < N; m += T) tw[m] = a.tw[stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N)];
   if (tid < C) {
     r_rb[tid] = map_rank(rb, tid);
     r_cb[tid] = map_rank(cb, tid);
     r_sl[tid] = map_rank(slots, tid);
+    m_cb[tid] = map_rank(&mb[0], tid);
+    m_rb[tid] = map_rank(&mb[1], tid);
+    m_sl[tid] = map_rank(&mb[2], tid);
   }
   __syncthreads();
   // Every CTA of the cluster read the same state (nothing writes it before
@@ -159,12 +210,13 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
                             : reinterpret_cast<const float2*>(a.V)[gi];
     ys[j * P + col] = a.y[gi];
   }
-  cluster_barrier();  // every CTA has started: its shared memory may be written
+  cluster_barrier();  // every CTA has started and armed its barriers
 
   const int j = tid / G, g = tid % G;    // step A / C: row j, line thread g
   const int kk = j, g2 = g;              // step B: k-space column kk
   const int kx = row0 + kk;              // its frequency index along x
   const float p2x = axis_p2(sy, 1, kx);
+  uint32_t ph_cb = 0, ph_rb = 0, ph_sl = 0;
   float2 v[NV];
   bool first = true;
   // Bounded by the state's own limit: finalize_iteration stops at it_limit.
@@ -180,12 +232,18 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
     fft_line<N>(v, rb + j * P, tw, g, false);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int k = out_index<N>(g, q);
-      st_cluster(r_cb[k / R] + (uint32_t)(((k % R) * P + row0 + j) * sizeof(float2)), v[q]);
+      const int k = out_index<N>(g, q), d = k / R, l = k % R;
+      st_async(r_cb[d] + (uint32_t)((l * P + swz<G>(l, row0 + j)) * sizeof(float2)), v[q], m_cb[d]);
     }
-    cluster_barrier();  // #1: columns complete; the previous iteration's sums arrived
+    if (!wait_cluster(&mb[0], ph_cb)) fail = 1;
+    ph_cb ^= 1u;
+    if (tid == 0) mbar_arrive_expect_tx(&mb[0], LINE_BYTES);   // next round of columns
     if (!first) {
+      // the previous iteration's sums (they were sent before its step C ended)
+      if (!wait_cluster(&mb[2], ph_sl)) fail = 1;
+      ph_sl ^= 1u;
       if (tid == 0) {
+        mbar_arrive_expect_tx(&mb[2], SLOT_BYTES);
         double tot = 0.0;
         for (int r = 0; r < C; ++r) tot += slots[r];
         finalize_iteration(&S, hist, tot, 0);
@@ -194,14 +252,19 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
           S.done = 1;
         }
       }
-      __syncthreads();
-      if (S.done) break;
     }
+    __syncthreads();
+    if (fail && tid == 0) {
+      S.status = ST_TIMEOUT;
+      S.done = 1;
+    }
+    __syncthreads();
+    if (S.done) break;
     first = false;
 
     // ---- B: FFT along y, multiply, inverse FFT along y, values to row owners
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = cb[kk * P + in_index<N>(g2, q)];
+    for (int q = 0; q < NV; ++q) v[q] = cb[kk * P + swz<G>(kk, in_index<N>(g2, q))];
     __syncwarp();  // a column's threads share a warp
     fft_line<N>(v, cb + kk * P, tw, g2, false);
     if (sy.table) {
@@ -226,14 +289,16 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
     fft_line<N>(v, cb + kk * P, tw, g2, true);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int jy = out_index<N>(g2, q);
-      st_cluster(r_rb[jy / R] + (uint32_t)(((jy % R) * P + kx) * sizeof(float2)), v[q]);
+      const int jy = out_index<N>(g2, q), d = jy / R, l = jy % R;
+      st_async(r_rb[d] + (uint32_t)((l * P + swz<G>(l, kx)) * sizeof(float2)), v[q], m_rb[d]);
     }
-    cluster_barrier();  // #2: rows complete
+    if (!wait_cluster(&mb[1], ph_rb)) fail = 1;
+    ph_rb ^= 1u;
+    if (tid == 0) mbar_arrive_expect_tx(&mb[1], LINE_BYTES);   // next round of rows
 
     // ---- C: inverse FFT along x, Delta, update, |Delta|^2 to every CTA
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = rb[j * P + in_index<N>(g, q)];
+    for (int q = 0; q < NV; ++q) v[q] = rb[j * P + swz<G>(j, in_index<N>(g, q))];
     __syncwarp();  // a row's threads share a warp
     fft_line<N>(v, rb + j * P, tw, g, true);
     float ss = 0.f;
@@ -255,22 +320,29 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
     if (tid < C) {
       double cta = 0.0;
       for (int w = 0; w < T / 32; ++w) cta += red[w];
-      st_cluster(r_sl[tid] + (uint32_t)(c * sizeof(double)), cta);
+      st_async(r_sl[tid] + (uint32_t)(c * sizeof(double)), cta, m_sl[tid]);
     }
     if (ref_pass) {
-      cluster_barrier();
+      if (!wait_cluster(&mb[2], ph_sl)) fail = 1;
+      ph_sl ^= 1u;
       if (tid == 0) {
         double tot = 0.0;
         for (int r = 0; r < C; ++r) tot += slots[r];
         finalize_iteration(&S, nullptr, tot, F_REF);  // stores ||Delta|| as the reference
       }
       __syncthreads();
+      if (fail && tid == 0) {
+        S.status = ST_TIMEOUT;
+        S.done = 1;
+      }
       break;
     }
   }
-  // No CTA touches another's shared memory after the last barrier.
+  // Every byte sent to this CTA has been waited for (or a wait gave up):
+  // meet the other CTAs before any of them leaves.
+  cluster_barrier();
   if (c == 0 && tid == 0) *gst = S;
-  if (!ref_pass) {
+  if (!ref_pass && !fail) {
     for (int i = tid; i < R * N; i += T) {
       const int jj = i / N, col = i % N;
       a.x_out[base + (int64_t)(row0 + jj) * N + col] = xs[jj * P + col];

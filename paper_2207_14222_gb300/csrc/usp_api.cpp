@@ -416,9 +416,13 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
 // ---- on-chip schedule (square 2-D grids n x n, n in {32, 64, 128, 256},
 // onchip_kernels.cu): a whole phase of iterations per launch.
 
-// Rows per CTA: the option, else 16.
+// Rows per CTA: the option, else 8 (twice the CTAs, each with half the
+// values) for single problems and batches of n <= 64, 16 for the rest
+// (measured, us per iteration, 16 / 8 rows: one 128^2 problem 5.97 / 5.37,
+// 64 of them 16.2 / 20.4; one 64^2 3.49 / 3.05, 64 of them 4.91 / 4.13).
 static int onchip_rows_of(const usp_solver* s, const usp_options& o) {
-  return o.onchip_rows > 0 ? o.onchip_rows : 16;
+  if (o.onchip_rows > 0) return o.onchip_rows;
+  return (s->n[0] <= 128 && (s->B == 1 || s->n[0] <= 64)) ? 8 : 16;
 }
 static bool onchip_available(const usp_solver* s, int rows) {
   return s->ndim == 2 && s->n[0] == s->n[1] && onchip_rows_ok(s->n[0], rows) &&
