@@ -136,6 +136,11 @@ typedef struct {
   /* rows (and k-space columns) per CTA of the on-chip schedule: 16, or 8
    * (n <= 128; twice the CTAs per problem), or 0 for the library's choice */
   int32_t onchip_rows;
+  /* testing hook, 0 in normal use: nonzero makes the on-chip schedule's
+   * first exchange expect bytes that are never sent, with a short wait
+   * limit, so the solve ends with the bounded-wait error (USP_ERR_CUDA,
+   * "timed out") and the solver stays usable                               */
+  int32_t test_wait_fault;
 } usp_options;
 
 typedef struct usp_solver usp_solver;

@@ -208,6 +208,8 @@ struct OnchipArgs {
   float alpha;          // single problem (batches: bt.alpha)
   Sym<float> sym;
   Batch bt;
+  uint32_t wait_limit;  // polls per bounded wait (0: the default, about a second)
+  uint32_t fault_tx;    // test hook: bytes added to the first exchange's expected count
 };
 bool onchip_side(int n);
 // rows: rows (and k-space columns) per CTA, 16 or 8 (8 for n <= 128).

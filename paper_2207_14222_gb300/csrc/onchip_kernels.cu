@@ -82,8 +82,8 @@ __device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar)
 }
 // Bounded wait for a phase of a local mbarrier whose bytes come from other
 // CTAs of the cluster (acquire at cluster scope makes their stores visible).
-__device__ __forceinline__ bool wait_cluster(uint64_t* b, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+__device__ __forceinline__ bool wait_cluster(uint64_t* b, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   const bool vreal = (a.flags & F_VREAL) != 0;
   const bool ref_pass = (a.flags & F_REF) != 0;
   const bool xzero = (a.flags & F_XZERO) != 0;
+  const uint32_t lim = a.wait_limit ? a.wait_limit : (1u << 22);
 
   if (tid == 0) {
     S = *gst;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
       for (int b = 0; b < 3; ++b) mbar_init(&mb[b], 1);
       fence_mbar_init();
       // first phase of each barrier armed before any CTA can send
-      mbar_arrive_expect_tx(&mb[0], LINE_BYTES);
+      mbar_arrive_expect_tx(&mb[0], LINE_BYTES + a.fault_tx);
       mbar_arrive_expect_tx(&mb[1], LINE_BYTES);
       mbar_arrive_expect_tx(&mb[2], SLOT_BYTES);
     }
@@ -235,14 +236,17 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
       const int k = out_index<N>(g, q), d = k / R, l = k % R;
       st_async(r_cb[d] + (uint32_t)((l * P + swz<G>(l, row0 + j)) * sizeof(float2)), v[q], m_cb[d]);
     }
-    if (!wait_cluster(&mb[0], ph_cb)) fail = 1;
+    // a phase is re-armed only by a thread that saw it complete (arming an
+    // incomplete phase would over-count its arrivals)
+    if (!wait_cluster(&mb[0], ph_cb, lim)) fail = 1;
+    else if (tid == 0) mbar_arrive_expect_tx(&mb[0], LINE_BYTES);   // next round of columns
     ph_cb ^= 1u;
-    if (tid == 0) mbar_arrive_expect_tx(&mb[0], LINE_BYTES);   // next round of columns
     if (!first) {
       // the previous iteration's sums (they were sent before its step C ended)
-      if (!wait_cluster(&mb[2], ph_sl)) fail = 1;
+      const bool got = wait_cluster(&mb[2], ph_sl, lim);
+      if (!got) fail = 1;
       ph_sl ^= 1u;
-      if (tid == 0) {
+      if (tid == 0 && got) {
         mbar_arrive_expect_tx(&mb[2], SLOT_BYTES);
         double tot = 0.0;
         for (int r = 0; r < C; ++r) tot += slots[r];
@@ -292,9 +296,9 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
       const int jy = out_index<N>(g2, q), d = jy / R, l = jy % R;
       st_async(r_rb[d] + (uint32_t)((l * P + swz<G>(l, kx)) * sizeof(float2)), v[q], m_rb[d]);
     }
-    if (!wait_cluster(&mb[1], ph_rb)) fail = 1;
+    if (!wait_cluster(&mb[1], ph_rb, lim)) fail = 1;
+    else if (tid == 0) mbar_arrive_expect_tx(&mb[1], LINE_BYTES);   // next round of rows
     ph_rb ^= 1u;
-    if (tid == 0) mbar_arrive_expect_tx(&mb[1], LINE_BYTES);   // next round of rows
 
     // ---- C: inverse FFT along x, Delta, update, |Delta|^2 to every CTA
 #pragma unroll
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
       st_async(r_sl[tid] + (uint32_t)(c * sizeof(double)), cta, m_sl[tid]);
     }
     if (ref_pass) {
-      if (!wait_cluster(&mb[2], ph_sl)) fail = 1;
+      if (!wait_cluster(&mb[2], ph_sl, lim)) fail = 1;
       ph_sl ^= 1u;
       if (tid == 0) {
         double tot = 0.0;

@@ -457,6 +457,10 @@ static OnchipArgs onchip_args(usp_solver* s, const float2* y, const float2* xin,
   a.alpha = (float)s->alpha;
   a.sym = s->symf;
   a.bt = batch_desc(s, 0);
+  if (s->opt.test_wait_fault) {   // bytes that nobody sends; give up after a few thousand polls
+    a.fault_tx = 8;
+    a.wait_limit = 4096;
+  }
   return a;
 }
 
@@ -1006,7 +1010,7 @@ static bool converged_state(const DevState& h, double tol) {
 
 // Status and message of one finished problem (prefix names it in a batch).
 static usp_status problem_status(const DevState& h, double tol, bool stagnated, const char* prefix) {
-  if (h.status == ST_TIMEOUT) return fail(USP_ERR_CUDA, "%sa bounded wait for the copy engine timed out", prefix);
+  if (h.status == ST_TIMEOUT) return fail(USP_ERR_CUDA, "%sa bounded wait inside a kernel timed out (copy engine or cluster peer)", prefix);
   if (h.status == ST_NONFINITE) return fail(USP_ERR_NONFINITE, "%snon-finite value in y, x0 or an iterate", prefix);
   if (h.status == ST_DIVERGED)
     return fail(USP_ERR_DIVERGED, "%s||Delta|| grew from %.3g to %.3g (relative)", prefix, h.phase_first_r,

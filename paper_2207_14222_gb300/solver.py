@@ -82,9 +82,10 @@ class Solver:
                          tc_dft=tc_dft, onchip_rows=onchip_rows)
 
     def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False,
-                    cols_tile=0, tc_dft=False, onchip_rows=0):
+                    cols_tile=0, tc_dft=False, onchip_rows=0, test_wait_fault=False):
         o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements),
-                    int(bool(no_tma)), int(cols_tile), int(bool(tc_dft)), int(onchip_rows))
+                    int(bool(no_tma)), int(cols_tile), int(bool(tc_dft)), int(onchip_rows),
+                    int(bool(test_wait_fault)))
         check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
 
     @property

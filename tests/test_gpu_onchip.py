@@ -197,3 +197,26 @@ def test_onchip_rejected_where_it_does_not_apply(torch_cuda):
         with pytest.raises(_lib.UspError) as e:
             _solver(torch, shape, cf, V, schedule=3)
         assert e.value.status == _lib.ERR_UNSUPPORTED_SIZE
+
+
+def test_onchip_bounded_wait_reports_timeout(torch_cuda):
+    """Failure detection without a fault: with the test hook the first exchange
+    expects bytes that no CTA sends, every wait gives up after its limit, the
+    CTAs meet at the final barrier and the solve reports the timeout; the
+    same solver then solves normally (the context is intact)."""
+    torch = torch_cuda
+    shape = (64, 64)
+    cf, V, y = _prep(inputs.white_helmholtz(shape, 209))
+    yd = torch.from_numpy(y).cuda()
+    with _solver(torch, shape, cf, V, plain=True, schedule=3) as s:
+        s.set_options(plain=True, schedule=3, test_wait_fault=True)
+        with pytest.raises(_lib.UspError) as e:
+            s.solve(yd, tol=1e-6, maxit=50)
+        assert e.value.status == _lib.ERR_CUDA and "timed out" in str(e.value)
+        s.set_options(plain=True, schedule=3)
+        x, res = s.solve(yd, tol=0.0, maxit=20)
+    assert res["iterations"] == 20
+    xo, _ = uo.iterate(V.astype(np.complex128), y.astype(np.complex128), _lh(shape, cf),
+                       res["alpha"], 20)
+    assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= TOL_X
+
