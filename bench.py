@@ -429,11 +429,12 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
 
 def variants_leg(args, torch, dev):
     """The block forms: the antisymmetrised Helmholtz problem with gain on
-    256 x 256 (K = 2) and flux-form diffusion with variable D on 128^3
-    (K = 4), plain FP32 Algorithm 1 to 1e-5.  Algorithmic bytes per point
-    and iteration: pre (read K x, K y, V; write K t) + each transform pass
-    (read and write K planes) + multiply (K read, K write) + post (read K u,
-    K x, V; write K x)."""
+    128 x 128 (K = 2; on chip, and with the passes for comparison) and
+    flux-form diffusion with variable D on 128^3 (K = 4), plain FP32
+    Algorithm 1 to 1e-5.  Algorithmic bytes per point and iteration of the
+    passes: pre (read K x, K y, V; write K t) + each transform pass (read and
+    write K planes) + multiply (K read, K write) + post (read K u, K x, V;
+    write K x)."""
     from paper_2207_14222_gb300 import canon, inputs
     from paper_2207_14222_gb300.solver import VariantSolver
     peak, _ = measured_hbm_peak()
@@ -448,6 +449,7 @@ def variants_leg(args, torch, dev):
     d = inputs.variable_diffusion((128, 128, 128), 0, sigma_px=4.0)
     cases.append(("flux_diffusion_128^3", (128, 128, 128),
                   canon.flux_diffusion(d["eta"], d["D"], np.real(d["S"])), 4, 8))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     for name, shape, cp, K, vb in cases:
         N = int(np.prod(shape))
         passes = 2 * len(shape)
@@ -455,17 +457,36 @@ def variants_leg(args, torch, dev):
         V = torch.from_numpy(cp["V"]).to(dev)
         y = torch.from_numpy(cp["y"]).to(dev)
         maxit = max(args.maxit, 100000)
-        with VariantSolver(shape, cp["kind"], cp["params"], V) as s:
-            s.solve(y, tol=1e-5, maxit=50)       # warm-up
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, r = s.solve(y, tol=1e-5, maxit=maxit)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-        gbs = bpp * N * r["iterations"] / dt / 1e9
-        out[name] = {"K": K, "iterations": r["iterations"], "converged": bool(r["converged"]),
-                     "s_to_1e-5": dt, "iter_per_s": r["iterations"] / dt,
-                     "bytes_per_point_iter": bpp, "GBps": gbs, "frac_of_peak": gbs / peak}
+        # square 2-D grids up to 128^2 run on chip by default; the passes beside them
+        scheds = [("onchip", 0), ("passes", 1)] if len(shape) == 2 and shape[0] == shape[1] else [("passes", 0)]
+        res = {}
+        for label, sched in scheds:
+            with VariantSolver(shape, cp["kind"], cp["params"], V, schedule=sched) as s:
+                s.solve(y, tol=1e-5, maxit=50)       # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, r = s.solve(y, tol=1e-5, maxit=maxit)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            d = {"iterations": r["iterations"], "converged": bool(r["converged"]), "s_to_1e-5": dt,
+                 "iter_per_s": r["iterations"] / dt}
+            if label == "onchip":
+                # ALU bound: K forward + inverse 2-D FFTs and the block pointwise steps
+                flop = (K * 2 * 5 * math.log2(N) + 40 * K) * N
+                ach = flop * r["iterations"] / dt / 1e12
+                peak_t = sms * FP32_LANES_PER_SM * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12
+                d.update({"bound": "alu", "flop_per_iteration": flop, "achieved_tflops": ach,
+                          "peak_tflops": peak_t, "frac": ach / peak_t})
+            else:
+                gbs = bpp * N * r["iterations"] / dt / 1e9
+                d.update({"bound": "hbm", "bytes_per_point_iter": bpp, "GBps": gbs, "frac_of_peak": gbs / peak})
+            res[label] = d
+        entry = {"K": K}
+        entry.update(res[scheds[0][0]])
+        if len(scheds) > 1:
+            entry["passes"] = res["passes"]
+            entry["speedup_vs_passes"] = res["passes"]["s_to_1e-5"] / res["onchip"]["s_to_1e-5"]
+        out[name] = entry
     return out
 
 

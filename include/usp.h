@@ -369,6 +369,15 @@ usp_status usp_variant_create(const usp_grid* grid, int32_t kind, const double* 
 usp_status usp_variant_solve(usp_variant* s, const void* y, void* x, int32_t use_x0,
                              double tol, int32_t maxit, double ref_norm, usp_result* out);
 
+/* Schedule of the variant's iterations (no counterpart in the paper): 0
+ * automatic -- square 2-D grids n x n, n in {32, 64, 128}, keep the K
+ * component fields of the problem in the shared memory of one thread-block
+ * cluster and run a whole solve per launch, other grids use the passes; 1
+ * the passes (pointwise kernels and the line / strided-axis transforms of
+ * every component plane); 3 the on-chip kernel (USP_ERR_UNSUPPORTED_SIZE
+ * where it does not apply).  Errors: USP_ERR_INVALID_ARG for other values. */
+usp_status usp_variant_set_schedule(usp_variant* s, int32_t schedule);
+
 /* Residual history of the last solve (as usp_residual_history). */
 usp_status usp_variant_history(const usp_variant* s, double* host_out, int32_t capacity,
                                int32_t* n_out);

@@ -115,6 +115,7 @@ _SIGNATURES = {
                                     c_double, _P(Result)]),
     "usp_variant_history": (c_int32, [c_void_p, _P(c_double), c_int32, _P(c_int32)]),
     "usp_variant_destroy": (None, [c_void_p]),
+    "usp_variant_set_schedule": (c_int32, [c_void_p, c_int32]),
     "usp_canon_antisymmetric": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_double,
                                           c_void_p, c_void_p, _P(c_double), _P(c_double)]),
     "usp_canon_flux_diffusion": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32,

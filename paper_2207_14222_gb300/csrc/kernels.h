@@ -196,7 +196,9 @@ cudaError_t launch_cols_tma(int n, int cols, const CUtensorMap& map, const ColsT
 // 128, 256}, resident in the shared memory of one cluster of n / 16 CTAs per
 // problem (onchip_kernels.cu).  One launch runs until every problem's state
 // says done; with F_REF it evaluates the reference norm only.
+enum : int { ONCHIP_SCALAR = 0, ONCHIP_ANTISYMMETRIC = 1, ONCHIP_FLUX = 2 };
 struct OnchipArgs {
+  int kind;             // ONCHIP_SCALAR, or a block form (K = 2 or 3 components as K planes)
   int flags;            // F_XZERO, F_REF, F_VREAL
   const float2* x_in;   // iterate in (not read with F_XZERO)
   float2* x_out;        // iterate out (may alias x_in; not written with F_REF)
@@ -206,7 +208,8 @@ struct OnchipArgs {
   DevState* st;
   double* hist;
   float alpha;          // single problem (batches: bt.alpha)
-  Sym<float> sym;
+  Sym<float> sym;       // block forms: ks, n and inv_n only
+  float bsym[4];        // block forms: (a_re, a_im, b_re, b_im) of l, or (alpha, beta, s)
   Batch bt;
   uint32_t wait_limit;  // polls per bounded wait (0: the default, about a second)
   uint32_t fault_tx;    // test hook: bytes added to the first exchange's expected count
@@ -214,9 +217,9 @@ struct OnchipArgs {
 bool onchip_side(int n);
 // rows: rows (and k-space columns) per CTA, 16 or 8 (8 for n <= 128).
 bool onchip_rows_ok(int n, int rows);
-// Clusters of the kernel for (n, rows) that fit on the device at once (0:
-// it cannot be launched here).
-int onchip_clusters(int n, int rows);
+// Clusters of the kernel for (n, rows, kind) that fit on the device at once
+// (0: it cannot be launched here or is not built for these sizes).
+int onchip_clusters(int n, int rows, int kind);
 cudaError_t launch_onchip(int n, int rows, const OnchipArgs& a, int problems, cudaStream_t s);
 
 // Fused rows pass of the pencil schedule as a persistent, bulk-copy staged

@@ -40,8 +40,16 @@
 namespace usp {
 namespace {
 
-template <int N, int RR>
+// Kinds of unknown: one component (the scalar form), or the block forms of
+// Sec. 2.2 (antisymmetrised, K = 2) and Sec. 3.2 (flux form in 2-D, K = 3).
+template <int KIND>
+struct Comps {
+  static constexpr int K = KIND == ONCHIP_SCALAR ? 1 : (KIND == ONCHIP_ANTISYMMETRIC ? 2 : 3);
+};
+
+template <int N, int RR, int KIND>
 struct OnchipCfg {
+  static constexpr int K = Comps<KIND>::K;   // components per point
   static constexpr int R = RR;               // rows (and k-space columns) per CTA
   static constexpr int C = N / R;            // CTAs per cluster
   static constexpr int G = Split<N>::G;      // threads per line
@@ -49,8 +57,11 @@ struct OnchipCfg {
   static constexpr int T = R * G;            // threads per CTA
   static constexpr int P = N + 8;            // line stride (float2): rows of a warp on both bank halves
   static constexpr int FIELD = R * P;        // float2 per resident array
-  // x, V, y, row buffer, column buffer, twiddles; then C + T/32 doubles
-  static constexpr size_t SMEM = sizeof(float2) * (5 * (size_t)FIELD + N) + sizeof(double) * (C + T / 32);
+  // K fields each of x, y, row buffer, column buffer; one of V; twiddles;
+  // then C + T/32 doubles
+  static constexpr size_t SMEM =
+      sizeof(float2) * ((4 * (size_t)K + 1) * FIELD + N) + sizeof(double) * (C + T / 32);
+  static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
   static_assert(Split<N>::N1 * Split<N>::N2 == N, "length");
   static_assert(T % 32 == 0, "whole warps");
   static_assert(C >= 2 && C <= 16, "cluster size");
@@ -120,6 +131,58 @@ __device__ __forceinline__ float2 linv_factor(float lr, float li, float inv_n) {
   return make_float2(dr * sc, -li * sc);
 }
 
+// B = I - V at one point, applied to the K components of `in` (v: the
+// point's entry of V: the complex potential; the antisymmetrised form's v,
+// B = [[1, conj(v)], [-v, 1]]; the flux form's (Vu, VJ), B = diag(1 - Vu,
+// (1 - VJ) I)).
+template <int KIND>
+__device__ __forceinline__ void apply_B(float2 v, const float2* in, float2* out) {
+  if constexpr (KIND == ONCHIP_SCALAR) {
+    const float br = 1.f - v.x;
+    out[0] = make_float2(fmaf(br, in[0].x, v.y * in[0].y), fmaf(br, in[0].y, -v.y * in[0].x));
+  } else if constexpr (KIND == ONCHIP_ANTISYMMETRIC) {
+    out[0] = make_float2(in[0].x + v.x * in[1].x + v.y * in[1].y, in[0].y + v.x * in[1].y - v.y * in[1].x);
+    out[1] = make_float2(in[1].x - (v.x * in[0].x - v.y * in[0].y), in[1].y - (v.x * in[0].y + v.y * in[0].x));
+  } else {
+    const float bu = 1.f - v.x, bj = 1.f - v.y;
+    out[0] = make_float2(bu * in[0].x, bu * in[0].y);
+    out[1] = make_float2(bj * in[1].x, bj * in[1].y);
+    out[2] = make_float2(bj * in[2].x, bj * in[2].y);
+  }
+}
+
+// (Lhat(p) + I)^-1 / N applied to the K spectral components T at one
+// frequency (py along axis 0, px along axis 1).  Block forms: b = (a_re,
+// a_im, b_re, b_im) of l = a |p|^2 + b, (L+I)^-1 = [[1, conj(l)], [-l, 1]] /
+// (1 + |l|^2); flux: b = (alpha, beta, s), the Schur complement of
+// [[alpha, i s p^T], [i s p, beta I]].
+template <int KIND>
+__device__ __forceinline__ void block_multiply(float2* T, float py, float px, const float* b, float inv_n) {
+  const float p2 = py * py + px * px;
+  if constexpr (KIND == ONCHIP_ANTISYMMETRIC) {
+    const float lr = fmaf(b[0], p2, b[2]), li = fmaf(b[1], p2, b[3]);
+    const float sc = __fdividef(inv_n, 1.f + lr * lr + li * li);
+    const float2 t0 = T[0], t1 = T[1];
+    T[0] = make_float2(sc * (t0.x + lr * t1.x + li * t1.y), sc * (t0.y + lr * t1.y - li * t1.x));
+    T[1] = make_float2(sc * (t1.x - (lr * t0.x - li * t0.y)), sc * (t1.y - (lr * t0.y + li * t0.x)));
+  } else if constexpr (KIND == ONCHIP_FLUX) {
+    const float al = b[0], be = b[1], sg = b[2];
+    const float S = al + sg * sg * p2 / be;
+    const float pk[2] = {py, px};
+    const float2 pT = make_float2(py * T[1].x + px * T[2].x, py * T[1].y + px * T[2].y);
+    const float iS = inv_n / S;
+    const float2 t0 = T[0];
+    T[0] = make_float2(iS * (t0.x + sg * pT.y / be), iS * (t0.y - sg * pT.x / be));
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float c1 = inv_n / be, c2 = sg * sg * pk[k] / (be * be * S) * inv_n;
+      const float c3 = sg * pk[k] / (be * S) * inv_n;
+      const float2 tk = T[1 + k];
+      T[1 + k] = make_float2(c1 * tk.x - c2 * pT.x + c3 * t0.y, c1 * tk.y - c2 * pT.y - c3 * t0.x);
+    }
+  }
+}
+
 // A line of N values held by its G threads (one warp holds whole lines, so
 // the exchange needs only warp synchronisation).
 template <int N>
@@ -144,19 +207,20 @@ __device__ __forceinline__ void fft_line(float2* v, float2* ex, const float2* tw
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
-template <int N, int RR>
-__global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a) {
-  typedef OnchipCfg<N, RR> K;
-  constexpr int C = K::C, R = K::R, G = K::G, NV = K::NV, T = K::T, P = K::P;
-  constexpr uint32_t LINE_BYTES = (uint32_t)(R * N * sizeof(float2));   // one round into rb or cb
+template <int N, int RR, int KIND>
+__global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipArgs a) {
+  typedef OnchipCfg<N, RR, KIND> Cf;
+  constexpr int K = Cf::K, C = Cf::C, R = Cf::R, G = Cf::G, NV = Cf::NV, T = Cf::T, P = Cf::P;
+  constexpr int F = Cf::FIELD;
+  constexpr uint32_t LINE_BYTES = (uint32_t)(K * R * N * sizeof(float2));   // one round into rb or cb
   constexpr uint32_t SLOT_BYTES = (uint32_t)(C * sizeof(double));
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* xs = reinterpret_cast<float2*>(smem_raw);
-  float2* vs = xs + K::FIELD;
-  float2* ys = vs + K::FIELD;
-  float2* rb = ys + K::FIELD;   // rows: k-space along x (exchange area of step A, input of step C)
-  float2* cb = rb + K::FIELD;   // k-space columns (input of step B)
-  float2* tw = cb + K::FIELD;
+  float2* xs = reinterpret_cast<float2*>(smem_raw);   // K fields (component k at xs + k F)
+  float2* ys = xs + K * F;
+  float2* vs = ys + K * F;      // one field: the point's entry of V
+  float2* rb = vs + F;          // K fields, rows: k-space along x (exchange of step A, input of step C)
+  float2* cb = rb + K * F;      // K fields, k-space columns (input of step B)
+  float2* tw = cb + K * F;
   double* slots = reinterpret_cast<double*>(tw + N);   // |Delta|^2 of each CTA
   double* red = slots + C;
   __shared__ DevState S;
@@ -167,7 +231,8 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   const int tid = threadIdx.x;
   const uint32_t c = cluster_rank();
   const int p = blockIdx.x / C;
-  const int64_t base = (int64_t)p * N * N;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t base = (int64_t)p * K * NN;
   DevState* gst = a.st + p;
   double* hist = c == 0 ? a.hist + (int64_t)p * a.bt.hist_stride : nullptr;
   const Sym<float> sy = problem_sym(a.sym, a.bt, p);
@@ -204,12 +269,16 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   if (S.done) return;
   const int row0 = (int)c * R;
   for (int i = tid; i < R * N; i += T) {
-    const int j = i / N, col = i % N;
-    const int64_t gi = base + (int64_t)(row0 + j) * N + col;
-    xs[j * P + col] = xzero ? make_float2(0.f, 0.f) : a.x_in[gi];
-    vs[j * P + col] = vreal ? make_float2(reinterpret_cast<const float*>(a.V)[gi], 0.f)
-                            : reinterpret_cast<const float2*>(a.V)[gi];
-    ys[j * P + col] = a.y[gi];
+    const int jj = i / N, col = i % N;
+    const int64_t gi = (int64_t)(row0 + jj) * N + col;   // within a plane
+    const int64_t vi = (int64_t)p * NN + gi;              // V: one entry per point
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      xs[k * F + jj * P + col] = xzero ? make_float2(0.f, 0.f) : a.x_in[base + k * NN + gi];
+      ys[k * F + jj * P + col] = a.y[base + k * NN + gi];
+    }
+    vs[jj * P + col] = vreal ? make_float2(reinterpret_cast<const float*>(a.V)[vi], 0.f)
+                             : reinterpret_cast<const float2*>(a.V)[vi];
   }
   cluster_barrier();  // every CTA has started and armed its barriers
 
@@ -217,24 +286,35 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   const int kk = j, g2 = g;              // step B: k-space column kk
   const int kx = row0 + kk;              // its frequency index along x
   const float p2x = axis_p2(sy, 1, kx);
+  const float px = sy.ks[1] * (float)signed_freq(kx, N);
   uint32_t ph_cb = 0, ph_rb = 0, ph_sl = 0;
-  float2 v[NV];
+  float2 v[K][NV];
   bool first = true;
   // Bounded by the state's own limit: finalize_iteration stops at it_limit.
   for (int iter = 0;; ++iter) {
-    // ---- A: t = (1 - V) x + y, FFT along x, k-space values to column owners
+    // ---- A: t = B x + y, FFT along x, k-space values to column owners
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       const int col = in_index<N>(g, q);
-      const float2 xv = xs[j * P + col], vv = vs[j * P + col], yv = ys[j * P + col];
-      const float br = 1.f - vv.x;
-      v[q] = make_float2(fmaf(br, xv.x, fmaf(vv.y, xv.y, yv.x)), fmaf(br, xv.y, fmaf(-vv.y, xv.x, yv.y)));
+      float2 xk[K], t[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) xk[k] = xs[k * F + j * P + col];
+      apply_B<KIND>(vs[j * P + col], xk, t);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float2 yv = ys[k * F + j * P + col];
+        v[k][q] = make_float2(t[k].x + yv.x, t[k].y + yv.y);
+      }
     }
-    fft_line<N>(v, rb + j * P, tw, g, false);
+#pragma unroll
+    for (int k = 0; k < K; ++k) fft_line<N>(v[k], rb + k * F + j * P, tw, g, false);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int k = out_index<N>(g, q), d = k / R, l = k % R;
-      st_async(r_cb[d] + (uint32_t)((l * P + swz<G>(l, row0 + j)) * sizeof(float2)), v[q], m_cb[d]);
+      const int kq = out_index<N>(g, q), d = kq / R, l = kq % R;
+      const uint32_t off = (uint32_t)((l * P + swz<G>(l, row0 + j)) * sizeof(float2));
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        st_async(r_cb[d] + off + (uint32_t)(k * F * sizeof(float2)), v[k][q], m_cb[d]);
     }
     // a phase is re-armed only by a thread that saw it complete (arming an
     // incomplete phase would over-count its arrivals)
@@ -268,33 +348,54 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
 
     // ---- B: FFT along y, multiply, inverse FFT along y, values to row owners
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = cb[kk * P + swz<G>(kk, in_index<N>(g2, q))];
-    __syncwarp();  // a column's threads share a warp
-    fft_line<N>(v, cb + kk * P, tw, g2, false);
-    if (sy.table) {
+    for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const float2 l = sy.table[out_index<N>(g2, q) * N + kx];
-        v[q] = cmul(v[q], linv_factor(l.x, l.y, sy.inv_n));
+      for (int q = 0; q < NV; ++q) v[k][q] = cb[k * F + kk * P + swz<G>(kk, in_index<N>(g2, q))];
+    __syncwarp();  // a column's threads share a warp
+#pragma unroll
+    for (int k = 0; k < K; ++k) fft_line<N>(v[k], cb + k * F + kk * P, tw, g2, false);
+    if constexpr (KIND == ONCHIP_SCALAR) {
+      if (sy.table) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const float2 l = sy.table[out_index<N>(g2, q) * N + kx];
+          v[0][q] = cmul(v[0][q], linv_factor(l.x, l.y, sy.inv_n));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const float p2 = p2x + axis_p2(sy, 0, out_index<N>(g2, q));
+          v[0][q] = cmul(v[0][q],
+                         linv_factor(fmaf(sy.a_re, p2, sy.b_re), fmaf(sy.a_im, p2, sy.b_im), sy.inv_n));
+        }
       }
     } else {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const float p2 = p2x + axis_p2(sy, 0, out_index<N>(g2, q));
-        v[q] = cmul(v[q], linv_factor(fmaf(sy.a_re, p2, sy.b_re), fmaf(sy.a_im, p2, sy.b_im), sy.inv_n));
+        float2 tq[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) tq[k] = v[k][q];
+        const float py = sy.ks[0] * (float)signed_freq(out_index<N>(g2, q), N);
+        block_multiply<KIND>(tq, py, px, a.bsym, sy.inv_n);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k][q] = tq[k];
       }
     }
-    {
-      float2 t[NV];
-      out_to_in<N>(v, t);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) v[q] = t[q];
+    for (int k = 0; k < K; ++k) {
+      float2 t[NV];
+      out_to_in<N>(v[k], t);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[k][q] = t[q];
+      fft_line<N>(v[k], cb + k * F + kk * P, tw, g2, true);
     }
-    fft_line<N>(v, cb + kk * P, tw, g2, true);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       const int jy = out_index<N>(g2, q), d = jy / R, l = jy % R;
-      st_async(r_rb[d] + (uint32_t)((l * P + swz<G>(l, kx)) * sizeof(float2)), v[q], m_rb[d]);
+      const uint32_t off = (uint32_t)((l * P + swz<G>(l, kx)) * sizeof(float2));
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        st_async(r_rb[d] + off + (uint32_t)(k * F * sizeof(float2)), v[k][q], m_rb[d]);
     }
     if (!wait_cluster(&mb[1], ph_rb, lim)) fail = 1;
     else if (tid == 0) mbar_arrive_expect_tx(&mb[1], LINE_BYTES);   // next round of rows
@@ -302,19 +403,29 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
 
     // ---- C: inverse FFT along x, Delta, update, |Delta|^2 to every CTA
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = rb[j * P + swz<G>(j, in_index<N>(g, q))];
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[k][q] = rb[k * F + j * P + swz<G>(j, in_index<N>(g, q))];
     __syncwarp();  // a row's threads share a warp
-    fft_line<N>(v, rb + j * P, tw, g, true);
+#pragma unroll
+    for (int k = 0; k < K; ++k) fft_line<N>(v[k], rb + k * F + j * P, tw, g, true);
     float ss = 0.f;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       const int col = out_index<N>(g, q);
-      const float2 xv = xs[j * P + col], vv = vs[j * P + col];
-      const float2 u = make_float2(v[q].x - xv.x, v[q].y - xv.y);
-      const float br = 1.f - vv.x;
-      const float2 d = make_float2(fmaf(br, u.x, vv.y * u.y), fmaf(br, u.y, -vv.y * u.x));
-      ss = fmaf(d.x, d.x, fmaf(d.y, d.y, ss));
-      if (!ref_pass) xs[j * P + col] = make_float2(fmaf(alpha, d.x, xv.x), fmaf(alpha, d.y, xv.y));
+      float2 xk[K], u[K], d[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        xk[k] = xs[k * F + j * P + col];
+        u[k] = make_float2(v[k][q].x - xk[k].x, v[k][q].y - xk[k].y);
+      }
+      apply_B<KIND>(vs[j * P + col], u, d);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        ss = fmaf(d[k].x, d[k].x, fmaf(d[k].y, d[k].y, ss));
+        if (!ref_pass)
+          xs[k * F + j * P + col] = make_float2(fmaf(alpha, d[k].x, xk[k].x), fmaf(alpha, d[k].y, xk[k].y));
+      }
     }
     double sd = (double)ss;
 #pragma unroll
@@ -349,55 +460,109 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR>::T, 1) k_onchip(OnchipArgs a)
   if (!ref_pass && !fail) {
     for (int i = tid; i < R * N; i += T) {
       const int jj = i / N, col = i % N;
-      a.x_out[base + (int64_t)(row0 + jj) * N + col] = xs[jj * P + col];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        a.x_out[base + k * NN + (int64_t)(row0 + jj) * N + col] = xs[k * F + jj * P + col];
     }
   }
 }
 
-template <int N, int RR>
+template <int N, int RR, int KIND>
 cudaError_t launch_n(const OnchipArgs& a, int problems, cudaStream_t s) {
-  typedef OnchipCfg<N, RR> K;
+  typedef OnchipCfg<N, RR, KIND> Cf;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(K::C * problems), 1, 1);
-  cfg.blockDim = dim3(K::T, 1, 1);
-  cfg.dynamicSmemBytes = K::SMEM;
+  cfg.gridDim = dim3((unsigned)(Cf::C * problems), 1, 1);
+  cfg.blockDim = dim3(Cf::T, 1, 1);
+  cfg.dynamicSmemBytes = Cf::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = K::C;
+  at[0].val.clusterDim.x = Cf::C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_onchip<N, RR>, a);
+  return cudaLaunchKernelEx(&cfg, k_onchip<N, RR, KIND>, a);
 }
 
-template <int N, int RR>
+template <int N, int RR, int KIND>
 int prepare_n() {
-  typedef OnchipCfg<N, RR> K;
-  if (cudaFuncSetAttribute(k_onchip<N, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM) !=
-      cudaSuccess)
+  typedef OnchipCfg<N, RR, KIND> Cf;
+  if (cudaFuncSetAttribute(k_onchip<N, RR, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Cf::SMEM) != cudaSuccess)
     return 0;
-  if (K::C > 8 && cudaFuncSetAttribute(k_onchip<N, RR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                      cudaSuccess)
+  if (Cf::C > 8 && cudaFuncSetAttribute(k_onchip<N, RR, KIND>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                        1) != cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(K::C, 1, 1);
-  cfg.blockDim = dim3(K::T, 1, 1);
-  cfg.dynamicSmemBytes = K::SMEM;
+  cfg.gridDim = dim3(Cf::C, 1, 1);
+  cfg.blockDim = dim3(Cf::T, 1, 1);
+  cfg.dynamicSmemBytes = Cf::SMEM;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = K::C;
+  at[0].val.clusterDim.x = Cf::C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_onchip<N, RR>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_onchip<N, RR, KIND>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
+}
+
+// The instantiations: (n, rows) for the scalar form; rows 8 and n <= 128 for
+// the block forms (their K fields per array would not fit otherwise).
+template <int KIND>
+bool instantiated(int n, int rows) {
+  if (KIND == ONCHIP_SCALAR) return onchip_rows_ok(n, rows);
+  return rows == 8 && (n == 32 || n == 64 || n == 128);
+}
+
+template <int KIND>
+int clusters_kind(int n, int rows) {
+  if (!instantiated<KIND>(n, rows)) return 0;
+  if (rows == 8) {
+    switch (n) {
+      case 32: return prepare_n<32, 8, KIND>();
+      case 64: return prepare_n<64, 8, KIND>();
+      case 128: return prepare_n<128, 8, KIND>();
+    }
+    return 0;
+  }
+  if constexpr (KIND == ONCHIP_SCALAR) {
+    switch (n) {
+      case 32: return prepare_n<32, 16, KIND>();
+      case 64: return prepare_n<64, 16, KIND>();
+      case 128: return prepare_n<128, 16, KIND>();
+      case 256: return prepare_n<256, 16, KIND>();
+    }
+  }
+  return 0;
+}
+
+template <int KIND>
+cudaError_t launch_kind(int n, int rows, const OnchipArgs& a, int problems, cudaStream_t s) {
+  if (!instantiated<KIND>(n, rows)) return cudaErrorInvalidValue;
+  if (rows == 8) {
+    switch (n) {
+      case 32: return launch_n<32, 8, KIND>(a, problems, s);
+      case 64: return launch_n<64, 8, KIND>(a, problems, s);
+      case 128: return launch_n<128, 8, KIND>(a, problems, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+  if constexpr (KIND == ONCHIP_SCALAR) {
+    switch (n) {
+      case 32: return launch_n<32, 16, KIND>(a, problems, s);
+      case 64: return launch_n<64, 16, KIND>(a, problems, s);
+      case 128: return launch_n<128, 16, KIND>(a, problems, s);
+      case 256: return launch_n<256, 16, KIND>(a, problems, s);
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -407,40 +572,20 @@ bool onchip_side(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 // rows: rows per CTA, 16 or 8 (8 only for n <= 128: at most 16 CTAs).
 bool onchip_rows_ok(int n, int rows) { return onchip_side(n) && (rows == 16 || (rows == 8 && n <= 128)); }
 
-int onchip_clusters(int n, int rows) {
-  if (!onchip_rows_ok(n, rows)) return 0;
-  if (rows == 8) {
-    switch (n) {
-      case 32: return prepare_n<32, 8>();
-      case 64: return prepare_n<64, 8>();
-      case 128: return prepare_n<128, 8>();
-    }
-    return 0;
-  }
-  switch (n) {
-    case 32: return prepare_n<32, 16>();
-    case 64: return prepare_n<64, 16>();
-    case 128: return prepare_n<128, 16>();
-    case 256: return prepare_n<256, 16>();
+int onchip_clusters(int n, int rows, int kind) {
+  switch (kind) {
+    case ONCHIP_SCALAR: return clusters_kind<ONCHIP_SCALAR>(n, rows);
+    case ONCHIP_ANTISYMMETRIC: return clusters_kind<ONCHIP_ANTISYMMETRIC>(n, rows);
+    case ONCHIP_FLUX: return clusters_kind<ONCHIP_FLUX>(n, rows);
   }
   return 0;
 }
 
 cudaError_t launch_onchip(int n, int rows, const OnchipArgs& a, int problems, cudaStream_t s) {
-  if (!onchip_rows_ok(n, rows)) return cudaErrorInvalidValue;
-  if (rows == 8) {
-    switch (n) {
-      case 32: return launch_n<32, 8>(a, problems, s);
-      case 64: return launch_n<64, 8>(a, problems, s);
-      case 128: return launch_n<128, 8>(a, problems, s);
-    }
-    return cudaErrorInvalidValue;
-  }
-  switch (n) {
-    case 32: return launch_n<32, 16>(a, problems, s);
-    case 64: return launch_n<64, 16>(a, problems, s);
-    case 128: return launch_n<128, 16>(a, problems, s);
-    case 256: return launch_n<256, 16>(a, problems, s);
+  switch (a.kind) {
+    case ONCHIP_SCALAR: return launch_kind<ONCHIP_SCALAR>(n, rows, a, problems, s);
+    case ONCHIP_ANTISYMMETRIC: return launch_kind<ONCHIP_ANTISYMMETRIC>(n, rows, a, problems, s);
+    case ONCHIP_FLUX: return launch_kind<ONCHIP_FLUX>(n, rows, a, problems, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -446,6 +446,7 @@ static bool use_onchip(const usp_solver* s) {
 static OnchipArgs onchip_args(usp_solver* s, const float2* y, const float2* xin, float2* xout,
                               int flags) {
   OnchipArgs a{};
+  a.kind = ONCHIP_SCALAR;
   a.flags = flags | (s->vreal ? F_VREAL : 0);
   a.x_in = xin;
   a.x_out = xout;
@@ -834,8 +835,8 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   if (count == 1 && s->ndim == 3 && s->n[1] == 256 && s->n[2] == 256)
     s->plane_clusters = plane_max_active_clusters();
   if (s->ndim == 2 && s->n[0] == s->n[1] && onchip_side(s->n[0])) {
-    s->onchip_clusters[0] = onchip_clusters(s->n[0], 8);
-    s->onchip_clusters[1] = onchip_clusters(s->n[0], 16);
+    s->onchip_clusters[0] = onchip_clusters(s->n[0], 8, ONCHIP_SCALAR);
+    s->onchip_clusters[1] = onchip_clusters(s->n[0], 16, ONCHIP_SCALAR);
   }
   *out = s;
   return USP_OK;

@@ -70,7 +70,38 @@ struct usp_variant {
   BlockArgs base{};
   std::vector<double> history;
   std::vector<Graph> graphs;
+  int schedule = 0;       // 0 automatic, 1 passes, 3 on-chip
+  int onchip = 0;         // co-resident clusters of the on-chip kernel (0: unavailable)
+  const float2* tw = nullptr;
 };
+
+// The on-chip kernel (onchip_kernels.cu) for square 2-D grids up to 128^2.
+static bool onchip_available(const usp_variant* s) { return s->onchip > 0; }
+static bool use_onchip(const usp_variant* s) {
+  return onchip_available(s) && (s->schedule == 0 || s->schedule == 3);
+}
+static cudaError_t enqueue_onchip(usp_variant* s, const float2* y, const float2* xin, float2* xout,
+                                  int flags, cudaStream_t strm) {
+  OnchipArgs o{};
+  o.kind = s->kind == USP_VARIANT_ANTISYMMETRIC ? ONCHIP_ANTISYMMETRIC : ONCHIP_FLUX;
+  o.flags = flags;
+  o.x_in = xin;
+  o.x_out = xout;
+  o.y = y;
+  o.V = s->V;
+  o.tw = s->tw;
+  o.st = s->st;
+  o.hist = s->hist;
+  o.alpha = (float)s->alpha;
+  o.sym.ndim = s->ndim;
+  for (int ax = 0; ax < 3; ++ax) {
+    o.sym.n[ax] = s->n[ax];
+    o.sym.ks[ax] = s->base.ks[ax];
+  }
+  o.sym.inv_n = s->base.inv_n;
+  for (int i = 0; i < 4; ++i) o.bsym[i] = s->base.sym[i];
+  return launch_onchip(s->n[0], 8, o, 1, strm);
+}
 
 static void free_graphs(usp_variant* s) {
   for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
@@ -229,12 +260,24 @@ extern "C" usp_status usp_variant_create(const usp_grid* grid, int32_t kind, con
   }
   s->alpha = alpha > 0.0 ? alpha : astar;
   a.alpha = (float)s->alpha;
+  s->tw = twiddle_table_f32();
+  if (s->ndim == 2 && s->n[0] == s->n[1] && s->n[0] <= 128 && s->tw)
+    s->onchip = onchip_clusters(s->n[0], 8, kind == USP_VARIANT_ANTISYMMETRIC ? ONCHIP_ANTISYMMETRIC : ONCHIP_FLUX);
 #undef VC_TRY
   *out = s;
   return USP_OK;
 }
 
 extern "C" void usp_variant_destroy(usp_variant* s) { vdestroy(s); }
+
+extern "C" usp_status usp_variant_set_schedule(usp_variant* s, int32_t schedule) {
+  if (!s) return vfail(USP_ERR_INVALID_ARG, "NULL solver");
+  if (schedule != 0 && schedule != 1 && schedule != 3) return vfail(USP_ERR_INVALID_ARG, "schedule must be 0, 1 or 3");
+  if (schedule == 3 && !onchip_available(s))
+    return vfail(USP_ERR_UNSUPPORTED_SIZE, "the on-chip schedule needs a 2-D grid n x n, n in {32, 64, 128}");
+  s->schedule = schedule;
+  return USP_OK;
+}
 
 static usp_status ensure_hist(usp_variant* s, int cap) {
   if (s->hist_cap >= cap) return USP_OK;
@@ -292,13 +335,20 @@ static usp_status vsolve(usp_variant* s, const float2* y, float2* x, int use_x0,
   h.tol = tol;
   V_TRY(cudaMemcpyAsync(s->st, s->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s->stream));
   bool skip = false;
+  const bool oc = use_onchip(s);
   if (use_x0 && !(ref_norm > 0)) {
     // Algorithm 1's denominator ||B (L+I)^-1 y||: Delta at x = 0, no update
-    V_TRY(enqueue_iteration(s, y, x, x, F_XZERO | F_REF, s->stream));
+    V_TRY(oc ? enqueue_onchip(s, y, x, x, F_XZERO | F_REF, s->stream)
+             : enqueue_iteration(s, y, x, x, F_XZERO | F_REF, s->stream));
     if ((st = read_state(s)) != USP_OK) return st;
     skip = h.done != 0;
   }
-  if (!skip) {
+  if (!skip && oc) {
+    // one launch runs the solve to the end
+    V_TRY(enqueue_onchip(s, y, x, x, use_x0 ? 0 : F_XZERO, s->stream));
+    if ((st = read_state(s)) != USP_OK) return st;
+    if (!h.done) return vfail(USP_ERR_CUDA, "on-chip solve ended with the state running");
+  } else if (!skip) {
     V_TRY(enqueue_iteration(s, y, x, x, use_x0 ? 0 : F_XZERO, s->stream));
     const int chunk = 8;
     cudaGraphExec_t ge = nullptr;
@@ -320,7 +370,8 @@ static usp_status vsolve(usp_variant* s, const float2* y, float2* x, int use_x0,
   const int nit = std::min(h.it, s->hist_cap);
   s->history.assign(nit, 0.0);
   if (nit > 0) V_TRY(cudaMemcpy(s->history.data(), s->hist, sizeof(double) * nit, cudaMemcpyDeviceToHost));
-  const bool converged = h.status != ST_NONFINITE && h.status != ST_DIVERGED && (h.it > 0 || h.ref == 0.0) &&
+  const bool converged = h.status != ST_NONFINITE && h.status != ST_DIVERGED && h.status != ST_TIMEOUT &&
+                         (h.it > 0 || h.ref == 0.0) &&
                          (h.last_r < tol || h.ref == 0.0);
   if (out) {
     out->iterations = h.it;
@@ -331,6 +382,7 @@ static usp_status vsolve(usp_variant* s, const float2* y, float2* x, int use_x0,
     out->ref_norm = h.ref;
     out->alpha = s->alpha;
   }
+  if (h.status == ST_TIMEOUT) return vfail(USP_ERR_CUDA, "a bounded wait inside a kernel timed out");
   if (h.status == ST_NONFINITE) return vfail(USP_ERR_NONFINITE, "non-finite value in y, x0 or an iterate");
   if (h.status == ST_DIVERGED)
     return vfail(USP_ERR_DIVERGED, "||Delta|| grew from %.3g to %.3g (relative)", h.phase_first_r, h.last_r);

@@ -336,7 +336,9 @@ class VariantSolver:
 
     KINDS = {"antisymmetric": 1, "flux": 2}
 
-    def __init__(self, shape, kind, params, V, alpha=0.0, dx=1.0, stream=None):
+    def __init__(self, shape, kind, params, V, alpha=0.0, dx=1.0, stream=None, schedule=0):
+        """schedule: 0 automatic (on chip for square 2-D grids up to 128^2), 1 the
+        passes, 3 on chip."""
         import torch
         if not V.is_cuda:
             raise ValueError("V must be a CUDA tensor")
@@ -359,6 +361,12 @@ class VariantSolver:
                                                 float(alpha), ctypes.c_void_p(stream),
                                                 ctypes.byref(h)))
         self._h = h
+        if schedule:
+            try:
+                check(_lib.lib().usp_variant_set_schedule(h, int(schedule)))
+            except Exception:
+                self.close()
+                raise
 
     def solve(self, y, x=None, tol=1e-5, maxit=20000, ref_norm=0.0, use_x0=False,
               allow_not_converged=True):

@@ -52,17 +52,17 @@ def _flux(shape, seed):
     return cp, co, ov.Flux(co)
 
 
-def _gpu(torch, shape, cp, n_iter=None, tol=0.0, maxit=None, alpha=0.0):
+def _gpu(torch, shape, cp, n_iter=None, tol=0.0, maxit=None, alpha=0.0, schedule=0):
     from paper_2207_14222_gb300.solver import VariantSolver
     with VariantSolver(shape, cp["kind"], cp["params"], torch.from_numpy(cp["V"]).cuda(),
-                       alpha=alpha) as s:
+                       alpha=alpha, schedule=schedule) as s:
         x, r = s.solve(torch.from_numpy(cp["y"]).cuda(), tol=tol,
                        maxit=maxit if maxit else n_iter)
         return x.cpu().numpy().astype(np.complex128), r, s.history()
 
 
-def _check(torch, shape, cp, op, n_iter):
-    xg, r, hg = _gpu(torch, shape, cp, n_iter)
+def _check(torch, shape, cp, op, n_iter, schedule=0):
+    xg, r, hg = _gpu(torch, shape, cp, n_iter, schedule=schedule)
     assert r["iterations"] == n_iter
     assert r["alpha"] == pytest.approx(op.alpha_star(), rel=1e-6)
     xo, ho = ov.iterate(op, cp["y"].astype(np.complex128), r["alpha"], n_iter)
@@ -84,6 +84,46 @@ def test_antisymmetric_trajectory(torch_cuda, shape):
 def test_flux_trajectory(torch_cuda, shape):
     cp, co, op = _flux(shape, 12)
     _check(torch_cuda, shape, cp, op, 40)
+
+
+# ---- square 2-D grids up to 128^2: the K component fields on chip (one
+# cluster per problem, one launch per solve), and the passes for comparison
+
+@pytest.mark.parametrize("kind, n, schedule", [
+    ("antisymmetric", 32, 3), ("antisymmetric", 64, 3), ("antisymmetric", 128, 3),
+    ("antisymmetric", 32, 1), ("flux", 32, 3), ("flux", 64, 3), ("flux", 128, 3), ("flux", 64, 1)])
+def test_variant_square_grids_by_schedule(torch_cuda, kind, n, schedule):
+    shape = (n, n)
+    cp, co, op = (_antisym if kind == "antisymmetric" else _flux)(shape, 16 + n)
+    _check(torch_cuda, shape, cp, op, 40, schedule=schedule)
+
+
+def test_variant_onchip_warm_start_and_reference_pass(torch_cuda):
+    """use_x0 without a reference norm: the reference pass runs on chip too,
+    and the second solve continues the first one's trajectory."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import VariantSolver
+    shape = (64, 64)
+    cp, co, op = _antisym(shape, 17)
+    y = torch.from_numpy(cp["y"]).cuda()
+    with VariantSolver(shape, cp["kind"], cp["params"], torch.from_numpy(cp["V"]).cuda(),
+                       schedule=3) as s:
+        x, r1 = s.solve(y, tol=0.0, maxit=15)
+        x, r2 = s.solve(y, x=x, use_x0=True, tol=0.0, maxit=15)
+    assert r2["ref_norm"] == pytest.approx(r1["ref_norm"], rel=1e-5)
+    xo, _ = ov.iterate(op, cp["y"].astype(np.complex128), r1["alpha"], 30)
+    assert _rel(x.cpu().numpy().astype(np.complex128), xo) <= TOL_X
+
+
+def test_variant_onchip_schedule_validation(torch_cuda):
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import VariantSolver
+    for shape in ((64, 32), (16, 16, 16), (256, 256), (96, 96)):
+        cp, _, _ = _antisym(shape, 18)
+        with pytest.raises(_lib.UspError) as e:
+            VariantSolver(shape, cp["kind"], cp["params"], torch.from_numpy(cp["V"]).cuda(),
+                          schedule=3)
+        assert e.value.status == _lib.ERR_UNSUPPORTED_SIZE
 
 
 def test_antisymmetric_converged_solution_solves_raw_problem(torch_cuda):
