@@ -93,12 +93,14 @@ __device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar)
 }
 // Bounded wait for a phase of a local mbarrier whose bytes come from other
 // CTAs of the cluster (acquire at cluster scope makes their stores visible).
+// Polls with test_wait (no suspension between polls: the CTA has nothing
+// else to run while it waits for its lines).
 __device__ __forceinline__ bool wait_cluster(uint64_t* b, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(b)), "r"(parity)
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
   const bool vreal = (a.flags & F_VREAL) != 0;
   const bool ref_pass = (a.flags & F_REF) != 0;
   const bool xzero = (a.flags & F_XZERO) != 0;
-  const uint32_t lim = a.wait_limit ? a.wait_limit : (1u << 22);
+  const uint32_t lim = a.wait_limit ? a.wait_limit : (1u << 26);   // about a second of polls
 
   if (tid == 0) {
     S = *gst;
