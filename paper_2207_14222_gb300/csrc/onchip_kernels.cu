@@ -26,6 +26,10 @@
 // before the test of the current one is read (its result is dropped if the
 // test stops the phase).
 //
+// The block forms (Sec. 2.2 antisymmetrised, K = 2; Sec. 3.2 flux form,
+// K = 3 in 2-D) run the same steps on K component planes: B = I - V is a
+// K x K matrix per point and (L+I)^-1 a K x K matrix per frequency.
+//
 // One launch runs a whole phase (until the state says done), one cluster per
 // problem of a batch.  Every wait is bounded; one that gives up records
 // ST_TIMEOUT and the CTAs meet at a final cluster barrier before they exit.
