@@ -369,19 +369,20 @@ __global__ void __launch_bounds__(RowsShape<T, N>::THREADS, RowsShape<T, N>::MIN
 
 // ------------------------------------------------------------ columns ---
 
+// Exchange rows XOR-swizzled as in the TMA column passes (bank halves).
 template <int N, bool INV, int COLS, typename V>
 __device__ __forceinline__ void fft_cols(V* v, V* ex, const V* tw, int g, int lane) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
   stage1<N, INV>(v, g, tw);
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * COLS + lane] = v[k1];
+  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + (g ^ (k1 & (N2 - 1)))) * COLS + lane] = v[k1];
   __syncthreads();
   V w[N1];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int k1 = g + G * s;
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * COLS + lane];
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + (n2 ^ (k1 & (N2 - 1)))) * COLS + lane];
   }
   __syncthreads();
   stage2<N, INV>(w);

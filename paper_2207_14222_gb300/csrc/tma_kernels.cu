@@ -25,20 +25,23 @@ namespace {
 
 constexpr int SLOTS = 3;
 
+// The exchange row of (k1, n2) is k1 N2 + (n2 ^ (k1 mod N2)): the warps'
+// reads (fixed n2, consecutive k1) then alternate between the two bank
+// halves of a 64-byte row instead of all landing on one.
 template <int N, bool INV, int COLS>
 __device__ __forceinline__ void fft_cols_slot(float2* v, float2* ex, const float2* tw, int g,
                                               int lane) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
   stage1<N, INV>(v, g, tw);
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + g) * COLS + lane] = v[k1];
+  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + (g ^ (k1 & (N2 - 1)))) * COLS + lane] = v[k1];
   __syncthreads();
   float2 w[N1];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int k1 = g + G * s;
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + n2) * COLS + lane];
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + (n2 ^ (k1 & (N2 - 1)))) * COLS + lane];
   }
   __syncthreads();
   stage2<N, INV>(w);
