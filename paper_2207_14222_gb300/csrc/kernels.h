@@ -46,7 +46,8 @@ enum : int {
   F_NOSTATE = 4,    // ignore the device state (stand-alone transforms)
   F_APPLY_A = 8,    // residual pass writes A x instead of y - A x
   F_VREAL = 16,     // V is float32 (real potential)
-  F_CBLOCK = 32     // z pass over the column-block layout of the fused schedule
+  F_CBLOCK = 32,    // z pass over the column-block layout of the fused schedule
+  F_REVERSE = 64    // strided-axis pass walks its tiles from the last one down
 };
 
 // Rows pass (transform along the contiguous last axis): a bit set of

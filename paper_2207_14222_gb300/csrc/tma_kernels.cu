@@ -111,9 +111,14 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
   // tiles of finished problems of a batch (their done flags do not change
   // during the pass): no loads are issued for them.  j counts the tiles
   // walked, which sets the ring slot and the barrier phase.
+  // Tile of walk step kk; with F_REVERSE the walk starts at the last tile
+  // (the end of the field, which the pass before this one wrote last and
+  // left in L2).
+  const bool rev = (a.flags & F_REVERSE) != 0;
+  auto tile_of = [&](int64_t kk) { return rev ? a.tiles - 1 - (t0 + kk * stride) : t0 + kk * stride; };
   auto active = [&](int64_t kk) {
     if (!batched || (a.flags & F_NOSTATE)) return true;
-    const int64_t tt = t0 + kk * stride;
+    const int64_t tt = tile_of(kk);
     return !a.st[int((tt / a.inner_blocks) / a.bt.outer_per)].done;
   };
   auto next_active = [&](int64_t kk) {
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
   };
   auto issue = [&](int64_t kk, int64_t jj) {   // thread 0: tile kk into slot jj
     const int sl = int(jj % SLOTS);
-    const int64_t tt = t0 + kk * stride;
+    const int64_t tt = tile_of(kk);
     mbar_arrive_expect_tx(&full[sl], TILE_BYTES);
     tma_load_3d(slots + sl * TILE, &map, int((tt % a.inner_blocks) * COLS), 0,
                 int(tt / a.inner_blocks), &full[sl]);
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
       break;
     }
     float2* slot = slots + s * TILE;
-    const int64_t t = t0 + k * stride;
+    const int64_t t = tile_of(k);
     const int64_t col = (t % a.inner_blocks) * COLS + lane;
     const int pb = batched ? int((t / a.inner_blocks) / a.bt.outer_per) : 0;
     const Sym<float> sy = problem_sym(a.sym, a.bt, pb);

@@ -367,9 +367,13 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
   if (nd == 2) {
     P.push_back({"cols0_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
   } else {
-    P.push_back({"cols1_fwd", 16.0, cols_pass_f32(s, 1, COL_FWD, cflags)});
+    // Both y passes walk from the last z-slab down: the forward one starts
+    // where the rows pass (increasing rows) stopped, and the inverse one
+    // stops at the first slab, where the next rows pass starts; the parts
+    // still in L2 are read first.
+    P.push_back({"cols1_fwd", 16.0, cols_pass_f32(s, 1, COL_FWD, cflags | F_REVERSE)});
     P.push_back({"cols0_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
-    P.push_back({"cols1_inv", 16.0, cols_pass_f32(s, 1, COL_INV, cflags)});
+    P.push_back({"cols1_inv", 16.0, cols_pass_f32(s, 1, COL_INV, cflags | F_REVERSE)});
   }
   if (ref) {
     r.mode = R_IN_BUF | R_INV | R_OUT_POST;
