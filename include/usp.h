@@ -111,7 +111,9 @@ typedef struct {
    *    has exactly the same Delta (A + B = L + I, Sec. 2.1); x = x + z.
    * 1: plain -- Algorithm 1 exactly: stop at tol or maxit.                 */
   int32_t plain;
-  /* 0: automatic (on-chip where it applies, else pencil);
+  /* 0: automatic (on-chip where it applies, except batches of 256^2
+   *    problems whose clusters do not all fit on the device at once; else
+   *    pencil);
    * 1: pencil schedule (one FFT axis per pass);
    * 2: fused 3-D schedule (two passes per iteration; 3-D grids nz x 256 x
    *    256, single problem);
