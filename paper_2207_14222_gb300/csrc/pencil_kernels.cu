@@ -415,7 +415,11 @@ __global__ void __launch_bounds__(ColsShape<N>::THREADS) k_cols(const ColsArgs<T
   V* rtw = tw + M;                          // W_N^m (radix stage), R > 1
   V* ex = rtw + (L::R > 1 ? N : 0);
 
-  const int64_t ib = blockIdx.x % a.inner_blocks, o = blockIdx.x / a.inner_blocks;
+  // F_REVERSE: the blocks take the tiles from the last one down (the blocks
+  // are dispatched in index order), so the end of the field, which the pass
+  // before wrote last, is read first
+  const int64_t bt = (a.flags & F_REVERSE) ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+  const int64_t ib = bt % a.inner_blocks, o = bt / a.inner_blocks;
   const int p = a.bt.count > 1 ? int(o / a.bt.outer_per) : 0;
   if (!(a.flags & F_NOSTATE) && a.st[p].done) return;
 

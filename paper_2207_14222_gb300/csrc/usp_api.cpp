@@ -365,7 +365,10 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
   }
   const int cflags = flags & ~F_XZERO & ~F_REF;
   if (nd == 2) {
-    P.push_back({"cols0_fwd_mul_inv", 16.0, cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags)});
+    // a batch's column pass walks from the last problem down: the rows pass
+    // wrote it last, and the next rows pass starts at the first problem
+    P.push_back({"cols0_fwd_mul_inv", 16.0,
+                 cols_pass_f32(s, 0, COL_FWD_MUL_INV, cflags | (s->B > 1 ? F_REVERSE : 0))});
   } else {
     // Both y passes walk from the last z-slab down: the forward one starts
     // where the rows pass (increasing rows) stopped, and the inverse one
