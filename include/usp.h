@@ -111,13 +111,14 @@ typedef struct {
    *    has exactly the same Delta (A + B = L + I, Sec. 2.1); x = x + z.
    * 1: plain -- Algorithm 1 exactly: stop at tol or maxit.                 */
   int32_t plain;
-  /* 0: automatic (on-chip where it applies, except batches of 256^2
-   *    problems whose clusters do not all fit on the device at once; else
-   *    pencil);
+  /* 0: automatic (on-chip where it applies, except batches of 192^2 and
+   *    256^2 problems whose clusters do not all fit on the device at once;
+   *    else pencil);
    * 1: pencil schedule (one FFT axis per pass);
    * 2: fused 3-D schedule (two passes per iteration; 3-D grids nz x 256 x
    *    256, single problem);
-   * 3: on-chip schedule (square 2-D grids n x n, n in {32, 64, 128, 256}):
+   * 3: on-chip schedule (square 2-D grids n x n, n in {32, 64, 96, 128,
+   *    192, 256}):
    *    each problem's fields stay in the shared memory of one thread-block
    *    cluster and one launch runs a whole phase of iterations.            */
   int32_t schedule;

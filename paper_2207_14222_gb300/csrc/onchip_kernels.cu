@@ -1,6 +1,6 @@
 // onchip_kernels.cu -- whole phases of Algorithm 1 for small square 2-D grids
-// (n x n, n in {32, 64, 128, 256}) with every field resident in the shared
-// memory of one thread-block cluster.
+// (n x n, n in {32, 64, 96, 128, 192, 256}) with every field resident in the
+// shared memory of one thread-block cluster.
 //
 // The pencil schedule streams the field through HBM two or three times per
 // iteration; at n <= 256 a field is at most 512 KiB, so those passes are
@@ -56,20 +56,24 @@ struct OnchipCfg {
   static constexpr int K = Comps<KIND>::K;   // components per point
   static constexpr int R = RR;               // rows (and k-space columns) per CTA
   static constexpr int C = N / R;            // CTAs per cluster
-  static constexpr int G = Split<N>::G;      // threads per line
-  static constexpr int NV = Split<N>::N1;    // values per thread
+  typedef Line<N> Ln;                        // N = R' M with a radix-R' outer stage (R' = 3 at 96, 192)
+  static constexpr int G = Ln::G;            // threads per line
+  static constexpr int NV = Ln::NV;          // values per thread
   static constexpr int T = R * G;            // threads per CTA
   static constexpr int P = N + 8;            // line stride (float2): rows of a warp on both bank halves
   static constexpr int FIELD = R * P;        // float2 per resident array
-  // K fields each of x, y, row buffer, column buffer; one of V; twiddles;
-  // then C + T/32 doubles
+  // K fields each of x, y, row buffer, column buffer; one of V; twiddles of
+  // the M-point stage and W_N^m of the outer stage; then C + T/32 doubles
   static constexpr size_t SMEM =
-      sizeof(float2) * ((4 * (size_t)K + 1) * FIELD + N) + sizeof(double) * (C + T / 32);
+      sizeof(float2) * ((4 * (size_t)K + 1) * FIELD + 2 * N) + sizeof(double) * (C + T / 32);
   static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
-  static_assert(Split<N>::N1 * Split<N>::N2 == N, "length");
+  static_assert(Ln::G * Ln::NV == N, "length");
   static_assert(T % 32 == 0, "whole warps");
   static_assert(C >= 2 && C <= 16, "cluster size");
-  static_assert(G <= 32 && 32 % G == 0, "the threads of a line share a warp");
+  static_assert(32 % Split<Ln::M>::G == 0, "the threads of an M-point sub-line share a warp");
+  // lines of a radix-3 outer stage straddle warps: their hand-offs take
+  // block barriers, those of the power-of-two lines warp barriers
+  static constexpr bool WARP_LINES = Ln::R == 1 && 32 % G == 0;
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -136,6 +140,15 @@ __device__ __forceinline__ float2 linv_factor(float lr, float li, float inv_n) {
   const float sc = __fdividef(inv_n, fmaf(dr, dr, li * li));
   return make_float2(dr * sc, -li * sc);
 }
+
+// Line transforms of one line held by its G threads (Line<N>): forward from
+// the spatial input order to the spectral output order, inverse from the
+// spectral input order to the spatial output order.  ex: the line's N-entry
+// exchange area; tw: M-point twiddles; rtw[m] = W_N^m (outer stage).
+template <int N>
+__device__ __forceinline__ void line_fwd(float2* v, float2* ex, const float2* tw, const float2* rtw, int l);
+template <int N>
+__device__ __forceinline__ void line_inv(float2* v, float2* ex, const float2* tw, const float2* rtw, int l);
 
 // B = I - V at one point, applied to the K components of `in` (v: the
 // point's entry of V: the complex potential; the antisymmetrised form's v,
@@ -213,9 +226,24 @@ __device__ __forceinline__ void fft_line(float2* v, float2* ex, const float2* tw
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
+template <int N>
+__device__ __forceinline__ void line_fwd(float2* v, float2* ex, const float2* tw, const float2* rtw, int l) {
+  typedef Line<N> Ln;
+  fft_line<Ln::M>(v, ex + (l / Ln::GM) * Ln::M, tw, l % Ln::GM, false);
+  if constexpr (Ln::R > 1) radix_fwd<N, 1>(v, ex, rtw, l, 0);
+}
+template <int N>
+__device__ __forceinline__ void line_inv(float2* v, float2* ex, const float2* tw, const float2* rtw, int l) {
+  typedef Line<N> Ln;
+  if constexpr (Ln::R > 1) radix_inv<N, 1>(v, ex, rtw, l, 0);
+  fft_line<Ln::M>(v, ex + (l / Ln::GM) * Ln::M, tw, l % Ln::GM, true);
+}
+
 template <int N, int RR, int KIND>
 __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipArgs a) {
   typedef OnchipCfg<N, RR, KIND> Cf;
+  typedef typename Cf::Ln Ln;
+  constexpr int MM = Ln::M;
   constexpr int K = Cf::K, C = Cf::C, R = Cf::R, G = Cf::G, NV = Cf::NV, T = Cf::T, P = Cf::P;
   constexpr int F = Cf::FIELD;
   constexpr uint32_t LINE_BYTES = (uint32_t)(K * R * N * sizeof(float2));   // one round into rb or cb
@@ -226,8 +254,9 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
   float2* vs = ys + K * F;      // one field: the point's entry of V
   float2* rb = vs + F;          // K fields, rows: k-space along x (exchange of step A, input of step C)
   float2* cb = rb + K * F;      // K fields, k-space columns (input of step B)
-  float2* tw = cb + K * F;
-  double* slots = reinterpret_cast<double*>(tw + N);   // |Delta|^2 of each CTA
+  float2* tw = cb + K * F;      // M-point stage-1 twiddles
+  float2* rtw = tw + N;         // W_N^m, m < N (outer stage)
+  double* slots = reinterpret_cast<double*>(rtw + N);   // |Delta|^2 of each CTA
   double* red = slots + C;
   __shared__ DevState S;
   __shared__ __align__(8) uint64_t mb[3];   // cb, rb, slots full
@@ -260,7 +289,13 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
       mbar_arrive_expect_tx(&mb[2], SLOT_BYTES);
     }
   }
-  for (int m = tid; m < N; m += T) tw[m] = a.tw[stage1_twiddle_exponent(m, Split<N>::N2) * (256 / N)];
+  for (int m = tid; m < MM; m += T) tw[m] = a.tw[stage1_twiddle_exponent(m, Split<MM>::N2) * (256 / MM)];
+  if (Ln::R > 1)
+    for (int m = tid; m < N; m += T) {
+      double sn, cs;
+      sincospi(-2.0 * m / N, &sn, &cs);   // W_N^m
+      rtw[m] = make_float2((float)cs, (float)sn);
+    }
   if (tid < C) {
     r_rb[tid] = map_rank(rb, tid);
     r_cb[tid] = map_rank(cb, tid);
@@ -301,7 +336,7 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
     // ---- A: t = B x + y, FFT along x, k-space values to column owners
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int col = in_index<N>(g, q);
+      const int col = Ln::sp_in(g, q);
       float2 xk[K], t[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) xk[k] = xs[k * F + j * P + col];
@@ -313,10 +348,10 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
       }
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) fft_line<N>(v[k], rb + k * F + j * P, tw, g, false);
+    for (int k = 0; k < K; ++k) line_fwd<N>(v[k], rb + k * F + j * P, tw, rtw, g);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int kq = out_index<N>(g, q), d = kq / R, l = kq % R;
+      const int kq = Ln::fr_out(g, q), d = kq / R, l = kq % R;
       const uint32_t off = (uint32_t)((l * P + swz<G>(l, row0 + j)) * sizeof(float2));
 #pragma unroll
       for (int k = 0; k < K; ++k)
@@ -356,21 +391,22 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int q = 0; q < NV; ++q) v[k][q] = cb[k * F + kk * P + swz<G>(kk, in_index<N>(g2, q))];
-    __syncwarp();  // a column's threads share a warp
+      for (int q = 0; q < NV; ++q) v[k][q] = cb[k * F + kk * P + swz<G>(kk, Ln::sp_in(g2, q))];
+    if (Cf::WARP_LINES) __syncwarp();  // a column's threads share a warp
+    else __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) fft_line<N>(v[k], cb + k * F + kk * P, tw, g2, false);
+    for (int k = 0; k < K; ++k) line_fwd<N>(v[k], cb + k * F + kk * P, tw, rtw, g2);
     if constexpr (KIND == ONCHIP_SCALAR) {
       if (sy.table) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          const float2 l = sy.table[out_index<N>(g2, q) * N + kx];
+          const float2 l = sy.table[Ln::fr_out(g2, q) * N + kx];
           v[0][q] = cmul(v[0][q], linv_factor(l.x, l.y, sy.inv_n));
         }
       } else {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          const float p2 = p2x + axis_p2(sy, 0, out_index<N>(g2, q));
+          const float p2 = p2x + axis_p2(sy, 0, Ln::fr_out(g2, q));
           v[0][q] = cmul(v[0][q],
                          linv_factor(fmaf(sy.a_re, p2, sy.b_re), fmaf(sy.a_im, p2, sy.b_im), sy.inv_n));
         }
@@ -381,7 +417,7 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
         float2 tq[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) tq[k] = v[k][q];
-        const float py = sy.ks[0] * (float)signed_freq(out_index<N>(g2, q), N);
+        const float py = sy.ks[0] * (float)signed_freq(Ln::fr_out(g2, q), N);
         block_multiply<KIND>(tq, py, px, a.bsym, sy.inv_n);
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k][q] = tq[k];
@@ -390,14 +426,14 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       float2 t[NV];
-      out_to_in<N>(v[k], t);
+      out_to_in<MM>(v[k], t);
 #pragma unroll
       for (int q = 0; q < NV; ++q) v[k][q] = t[q];
-      fft_line<N>(v[k], cb + k * F + kk * P, tw, g2, true);
+      line_inv<N>(v[k], cb + k * F + kk * P, tw, rtw, g2);
     }
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int jy = out_index<N>(g2, q), d = jy / R, l = jy % R;
+      const int jy = Ln::sp_out(g2, q), d = jy / R, l = jy % R;
       const uint32_t off = (uint32_t)((l * P + swz<G>(l, kx)) * sizeof(float2));
 #pragma unroll
       for (int k = 0; k < K; ++k)
@@ -411,14 +447,15 @@ __global__ void __launch_bounds__(OnchipCfg<N, RR, KIND>::T, 1) k_onchip(OnchipA
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int q = 0; q < NV; ++q) v[k][q] = rb[k * F + j * P + swz<G>(j, in_index<N>(g, q))];
-    __syncwarp();  // a row's threads share a warp
+      for (int q = 0; q < NV; ++q) v[k][q] = rb[k * F + j * P + swz<G>(j, Ln::fr_in(g, q))];
+    if (Cf::WARP_LINES) __syncwarp();  // a row's threads share a warp
+    else __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) fft_line<N>(v[k], rb + k * F + j * P, tw, g, true);
+    for (int k = 0; k < K; ++k) line_inv<N>(v[k], rb + k * F + j * P, tw, rtw, g);
     float ss = 0.f;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const int col = out_index<N>(g, q);
+      const int col = Ln::sp_out(g, q);
       float2 xk[K], u[K], d[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -526,6 +563,7 @@ bool instantiated(int n, int rows) {
   if (KIND == ONCHIP_SCALAR) return onchip_rows_ok(n, rows);
   return rows == 8 && (n == 32 || n == 64 || n == 128);
 }
+// (the radix-3 sides 96 and 192 are built for the scalar form only)
 
 template <int KIND>
 int clusters_kind(int n, int rows) {
@@ -536,13 +574,17 @@ int clusters_kind(int n, int rows) {
       case 64: return prepare_n<64, 8, KIND>();
       case 128: return prepare_n<128, 8, KIND>();
     }
+    if constexpr (KIND == ONCHIP_SCALAR)
+      if (n == 96) return prepare_n<96, 8, KIND>();
     return 0;
   }
   if constexpr (KIND == ONCHIP_SCALAR) {
     switch (n) {
       case 32: return prepare_n<32, 16, KIND>();
       case 64: return prepare_n<64, 16, KIND>();
+      case 96: return prepare_n<96, 16, KIND>();
       case 128: return prepare_n<128, 16, KIND>();
+      case 192: return prepare_n<192, 16, KIND>();
       case 256: return prepare_n<256, 16, KIND>();
     }
   }
@@ -558,13 +600,17 @@ cudaError_t launch_kind(int n, int rows, const OnchipArgs& a, int problems, cuda
       case 64: return launch_n<64, 8, KIND>(a, problems, s);
       case 128: return launch_n<128, 8, KIND>(a, problems, s);
     }
+    if constexpr (KIND == ONCHIP_SCALAR)
+      if (n == 96) return launch_n<96, 8, KIND>(a, problems, s);
     return cudaErrorInvalidValue;
   }
   if constexpr (KIND == ONCHIP_SCALAR) {
     switch (n) {
       case 32: return launch_n<32, 16, KIND>(a, problems, s);
       case 64: return launch_n<64, 16, KIND>(a, problems, s);
+      case 96: return launch_n<96, 16, KIND>(a, problems, s);
       case 128: return launch_n<128, 16, KIND>(a, problems, s);
+      case 192: return launch_n<192, 16, KIND>(a, problems, s);
       case 256: return launch_n<256, 16, KIND>(a, problems, s);
     }
   }
@@ -573,7 +619,7 @@ cudaError_t launch_kind(int n, int rows, const OnchipArgs& a, int problems, cuda
 
 }  // namespace
 
-bool onchip_side(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+bool onchip_side(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256; }
 
 // rows: rows per CTA, 16 or 8 (8 only for n <= 128: at most 16 CTAs).
 bool onchip_rows_ok(int n, int rows) { return onchip_side(n) && (rows == 16 || (rows == 8 && n <= 128)); }

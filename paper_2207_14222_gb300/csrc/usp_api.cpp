@@ -424,12 +424,13 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
 // onchip_kernels.cu): a whole phase of iterations per launch.
 
 // Rows per CTA: the option, else 8 (twice the CTAs, each with half the
-// values) for single problems and batches of n <= 64, 16 for the rest
+// values) for single problems and batches of n <= 96, 16 for the rest
 // (measured, us per iteration, 16 / 8 rows: one 128^2 problem 5.97 / 5.37,
-// 64 of them 16.2 / 20.4; one 64^2 3.49 / 3.05, 64 of them 4.91 / 4.13).
+// 64 of them 16.2 / 20.4; one 64^2 3.49 / 3.05, 64 of them 4.91 / 4.13;
+// one 96^2 8.6 / 6.7, 70 of them 22.8 / 21.2).
 static int onchip_rows_of(const usp_solver* s, const usp_options& o) {
   if (o.onchip_rows > 0) return o.onchip_rows;
-  return (s->n[0] <= 128 && (s->B == 1 || s->n[0] <= 64)) ? 8 : 16;
+  return (s->n[0] <= 128 && (s->B == 1 || s->n[0] <= 96)) ? 8 : 16;
 }
 static bool onchip_available(const usp_solver* s, int rows) {
   return s->ndim == 2 && s->n[0] == s->n[1] && onchip_rows_ok(s->n[0], rows) &&
@@ -438,10 +439,10 @@ static bool onchip_available(const usp_solver* s, int rows) {
 static bool onchip_supported(const usp_solver* s) { return onchip_available(s, onchip_rows_of(s, s->opt)); }
 // Schedule 3 forces the on-chip kernels, schedule 1 the pencil passes.  The
 // automatic choice (0) takes on-chip where it applies unless the problems'
-// clusters do not all fit on the device at once and each holds 16 SMs' worth
-// of shared memory (n = 256): there the passes keep more SMs busy (measured:
-// 64 problems of 256^2, 75 us per pencil iteration against 108 us on chip;
-// 64 of 128^2, 35 us against 17 us).
+// clusters do not all fit on the device at once and each holds 12-16 SMs'
+// worth of shared memory (n = 192, 256): there the passes keep more SMs busy
+// (measured: 64 problems of 256^2, 75 us per pencil iteration against 108 us
+// on chip; 70 of 192^2, 80 against 122 us; 64 of 128^2, 35 against 17 us).
 static bool use_onchip(const usp_solver* s) {
   if (!onchip_supported(s)) return false;
   if (s->opt.schedule == 3) return true;
@@ -874,7 +875,8 @@ extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* o
     return fail(USP_ERR_INVALID_ARG, "onchip_rows must be 0, 8 or 16");
   if (opt->schedule == 3 && !onchip_available(s, onchip_rows_of(s, *opt)))
     return fail(USP_ERR_UNSUPPORTED_SIZE,
-                "the on-chip schedule needs a 2-D grid n x n, n in {32, 64, 128, 256} (8 rows per CTA: n <= 128)");
+                "the on-chip schedule needs a 2-D grid n x n, n in {32, 64, 96, 128, 192, 256} (8 rows per CTA: "
+                "n <= 128)");
   free_graphs(s);  // captured graphs follow the old schedule
   s->opt = *opt;
   return USP_OK;

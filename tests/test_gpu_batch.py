@@ -80,7 +80,9 @@ def _check_trajectories(torch, shape, probs, n_iter, vreal=False, schedule=0):
     ((128, 128), 3, 1),        # staged line pass, 2 tiles per problem
     ((16, 64, 64), 2, 0),
     ((8, 128, 128), 2, 0),     # staged line and column passes
-    ((96, 96), 3, 0),          # radix-3 lines
+    ((96, 96), 3, 1),          # radix-3 lines
+    ((96, 96), 3, 0),          # on-chip, radix-3 lines
+    ((192, 192), 2, 0),
     ((512, 64), 2, 0),         # radix-2 outer stage on the strided axis
     ((64, 64), 5, 0),          # on-chip: one cluster per problem
     ((128, 128), 3, 0),

@@ -60,7 +60,7 @@ def _trajectory(torch, shape, prob, n_iter, vreal=False, **kw):
     return xg
 
 
-@pytest.mark.parametrize("n", [32, 64, 128, 256])
+@pytest.mark.parametrize("n", [32, 64, 96, 128, 192, 256])
 def test_onchip_trajectory(torch_cuda, n):
     _trajectory(torch_cuda, (n, n), inputs.white_helmholtz((n, n), 200 + n), 40)
 
@@ -192,7 +192,7 @@ def test_onchip_deterministic(torch_cuda):
 
 def test_onchip_rejected_where_it_does_not_apply(torch_cuda):
     torch = torch_cuda
-    for shape in ((64, 128), (96, 96), (16, 16), (8, 32, 32)):
+    for shape in ((64, 128), (384, 384), (16, 16), (8, 32, 32)):
         cf, V, y = _prep(inputs.white_helmholtz(shape, 208))
         with pytest.raises(_lib.UspError) as e:
             _solver(torch, shape, cf, V, schedule=3)
@@ -219,4 +219,10 @@ def test_onchip_bounded_wait_reports_timeout(torch_cuda):
     xo, _ = uo.iterate(V.astype(np.complex128), y.astype(np.complex128), _lh(shape, cf),
                        res["alpha"], 20)
     assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= TOL_X
+
+
+@pytest.mark.parametrize("n, rows", [(96, 8), (96, 16)])
+def test_onchip_radix3_rows_per_cta(torch_cuda, n, rows):
+    """Radix-3 lines (96 = 3 x 32) with 8 or 16 rows per CTA (12 or 6 CTAs)."""
+    _trajectory(torch_cuda, (n, n), inputs.white_helmholtz((n, n), 210 + rows), 30, onchip_rows=rows)
 
