@@ -79,6 +79,18 @@ def test_create_rejects_bad_arguments(L):
     assert "alpha" in _lib.last_error()
 
 
+def test_null_handles_are_rejected(L):
+    """Entry points that take a solver handle refuse NULL without touching the
+    device (no GPU here)."""
+    o = _lib.Options()
+    assert L.usp_solver_set_options(None, ctypes.byref(o)) == _lib.ERR_INVALID_ARG
+    assert L.usp_variant_set_schedule(None, 0) == _lib.ERR_INVALID_ARG
+    a = ctypes.c_double()
+    assert L.usp_solver_alpha(None, ctypes.byref(a)) == _lib.ERR_INVALID_ARG
+    n = ctypes.c_int32()
+    assert L.usp_residual_history(None, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID_ARG
+
+
 def test_table_symbol_rejections(L):
     """A tabulated symbol needs a table, one problem, and a known kind; the
     allocation-free entry point takes the quadratic symbol only."""
