@@ -33,8 +33,15 @@ class Solver:
             potential), copied at construction.
     alpha : step size; <= 0 selects Re[B^-1] = min Re 1/(1 - V).
     plain : True runs Algorithm 1 exactly (no FP64 refinement).
-    schedule : 0 auto, 1 pencil passes, 2 fused two-pass 3-D schedule.
+    schedule : 0 auto, 1 pencil passes, 2 fused two-pass 3-D schedule,
+            3 on-chip (square 2-D grids of side 32, 64, 96, 128, 192, 256:
+            the fields stay in one thread-block cluster's shared memory).
     no_tma : True loads the strided-axis passes with plain global accesses.
+    cols_tile : columns per staged strided-axis tile (8, 16, 32; 0 default).
+    tc_dft : True runs the 256-point strided-axis transforms on the tensor cores.
+    lhat_table : complex64 CUDA tensor of Lhat on the grid's frequencies (FFT
+            order) instead of a |p|^2 + b.
+    onchip_rows : rows per CTA of the on-chip schedule (8, 16; 0 default).
     """
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
