@@ -216,6 +216,18 @@ def onchip_roofline(passes, problems, n, torch, dev, sm_mhz=None):
             % (sms, FP32_LANES_PER_SM, mhz), "frac": achieved / peak}
 
 
+def schedule_efficiency(passes, points, vreal, iteration_ms, peak):
+    """The iteration's floor -- read x, y and V, write x: 32 bytes per point
+    (28 with a real V) -- against the bytes the schedule moves per iteration:
+    their ratio, and the iterations/s the floor would allow at the peak."""
+    floor = 28.0 if vreal else 32.0
+    sched = sum(p["bytes"] for p in passes) / points
+    return {"floor_bytes_per_point": floor, "schedule_bytes_per_point": sched,
+            "schedule_efficiency": floor / sched if sched > 0 else None,
+            "floor_iter_per_s": peak * 1e9 / (floor * points),
+            "iter_per_s_at_iteration_ms": 1e3 / iteration_ms}
+
+
 # Sources of the pencil-schedule kernels whose ncu traffic is recorded.
 PENCIL_SOURCES = ("fft_core.cuh", "iteration_state.cuh", "kernels.h", "pencil_kernels.cu",
                   "tma.cuh", "tma_kernels.cu")
@@ -378,6 +390,8 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
             "passes": [{"name": p["name"], "ms": round(p["ms"], 5),
                         "GBps": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)} for p in passes],
         }
+        out["roofline"].update(schedule_efficiency(passes, int(np.prod(shape)), V.dtype == torch.float32,
+                                                   per_it_ms, peak))
     # end to end through the host API: pinned V, y in; x out
     Vh = V.cpu().pin_memory()
     yh = y.cpu().pin_memory()
