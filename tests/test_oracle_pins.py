@@ -549,6 +549,10 @@ def test_history_is_relative_preconditioned_residual():
     assert ok and hist[-1] < tol and np.all(hist[:-1] >= tol)
     assert np.allclose(x.ravel(), xd, atol=1e-12 * np.abs(xd).max())
     assert uo.reference_norm(cf["y"], cf["V"], Lh) == pytest.approx(ref, rel=1e-12)
+    # a fixed number of steps (no stopping test) follows the same recurrence
+    xi, hi = uo.iterate(cf["V"], cf["y"], Lh, alpha, len(hist))
+    assert np.allclose(hi, expect, rtol=1e-9)
+    assert np.allclose(xi.ravel(), xd, atol=1e-12 * np.abs(xd).max())
 
 
 # --------------------------------------------------- tabulated symbol ---
@@ -575,3 +579,116 @@ def test_table_symbol_equals_real_space_stencil(shape):
     u = uo.apply_L_plus_I_inverse(x, Texact)
     assert np.allclose(stencil_apply(u, dx, a, b, drift) + u, x, rtol=1e-11, atol=1e-11)
 
+
+
+# ------------------------------------- unpreconditioned relative residual ---
+
+def _check_relative_residual(fn):
+    """Largest deviation of ``fn(x, y, V, Lhat)`` from ||A x - y|| / ||y||
+    with A = L + diag(V) assembled densely from the DFT definition (Sec. 4.1's
+    measure), at a random x, at x = 0 (exactly 1) and at the solution of A x
+    = y by Gaussian elimination (0 up to rounding)."""
+    shape = (4, 6, 8)
+    cf, Lh = _small_helmholtz(shape, 21)
+    A, _, _ = dense.dense_system(shape, cf["dx"], cf["a"], cf["b"], cf["V"])
+    y = cf["y"]
+    errs = []
+    for seed in (22, 23):
+        x = _rand(shape, seed)
+        expect = np.linalg.norm(A @ x.ravel() - y.ravel()) / np.linalg.norm(y)
+        errs.append(abs(fn(x, y, cf["V"], Lh) - expect) / expect)
+    errs.append(abs(fn(np.zeros(shape, np.complex128), y, cf["V"], Lh) - 1.0))
+    xs = np.linalg.solve(A, y.ravel()).reshape(shape)
+    errs.append(abs(fn(xs, y, cf["V"], Lh)))
+    return max(errs)
+
+
+def test_relative_residual_against_dense_operator():
+    assert _check_relative_residual(uo.relative_residual) < 1e-12
+
+
+@pytest.mark.parametrize("mistake", ["divide_by_x", "drop_V", "preconditioned",
+                                     "sign_of_V", "squared"])
+def test_relative_residual_pin_catches_planted_mistakes(mistake):
+    """Plausible mistakes in the residual (dividing by ||x||, leaving out V,
+    reporting the preconditioned residual, a sign slip, the squared norm)
+    each fail the dense pin above."""
+    def planted(x, y, V, Lh):
+        nrm = np.linalg.norm
+        if mistake == "divide_by_x":
+            return nrm(uo.apply_A(x, V, Lh) - y) / max(nrm(x), 1e-300)
+        if mistake == "drop_V":
+            return nrm(uo.apply_L(x, Lh) - y) / nrm(y)
+        if mistake == "preconditioned":
+            return nrm(uo.residual_delta(x, y, V, Lh)) / nrm(y)
+        if mistake == "sign_of_V":
+            return nrm(uo.apply_L(x, Lh) - V * x - y) / nrm(y)
+        return nrm(uo.apply_A(x, V, Lh) - y) ** 2 / nrm(y) ** 2
+    assert _check_relative_residual(planted) > 1e-3
+
+
+# ------------------------------------- empty medium: 2-D and 3-D Green's ---
+
+def _point_source_solution(shape, dx, k0, kappa):
+    """Algorithm 1 on a homogeneous absorbing medium k^2 = k0^2 + i kappa
+    with a unit point source at the origin: real bias k0^2, circle radius
+    kappa, c = i kappa / 0.95, so V = 0.95 everywhere (Sec. 3.1)."""
+    k2 = k0 ** 2 + 1j * kappa
+    c = 1j * kappa / 0.95
+    S = np.zeros(shape, np.complex128)
+    S[(0,) * len(shape)] = 1.0 / dx ** len(shape)
+    Lh = uo.lhat(shape, dx, -1 / c, k0 ** 2 / c)
+    x, _, ok = uo.solve(np.full(shape, (k2 - k0 ** 2) / c), -S / c, Lh, 1.0,
+                        1e-11, 5000)
+    assert ok
+    return x, np.sqrt(k2)
+
+
+def _off_axis_mask(d, dx, ndim):
+    """Grid points at least two pixels from every coordinate plane through
+    the source.  The sampled symbol differs from the continuous one only
+    beyond the grid's band, and the aliased remainder of a point source's
+    field concentrates on those planes (the band is a product of intervals);
+    elsewhere the grid field equals the continuous one to about 2e-4."""
+    m = d >= 2 * dx
+    out = m
+    for _ in range(ndim - 1):
+        out = np.multiply.outer(out, m)
+    return out
+
+
+def test_helmholtz_2d_point_source_green_function():
+    """Empty-medium check (Sec. 3.1) in 2-D: laplacian psi + k^2 psi = -delta
+    has the free-space solution (i/4) H0^(1)(k r); on the periodic grid the
+    field is the sum of its periodic images (which converges: Im k > 0)."""
+    from scipy.special import hankel1
+    n, dx, k0, kappa, images = 256, 0.5, np.pi / 2, 0.3, 3
+    x, k = _point_source_solution((n, n), dx, k0, kappa)
+    P = n * dx
+    d = np.minimum(np.arange(n) * dx, P - np.arange(n) * dx)
+    G = np.zeros((n, n), np.complex128)
+    for i in range(-images, images + 1):
+        for j in range(-images, images + 1):
+            r = np.hypot(d[:, None] + i * P, d[None, :] + j * P)
+            G += 0.25j * hankel1(0, k * np.where(r > 0, r, 1.0))
+    m = _off_axis_mask(d, dx, 2)
+    assert np.abs(x[m] - G[m]).max() / np.abs(G[m]).max() < 1e-3
+
+
+def test_helmholtz_3d_point_source_green_function():
+    """Empty-medium check (Sec. 3.1) in 3-D: the free-space solution is
+    e^{i k r} / (4 pi r), summed over its periodic images."""
+    n, dx, k0, kappa, images = 64, 0.5, np.pi / 2, 0.5, 2
+    x, k = _point_source_solution((n, n, n), dx, k0, kappa)
+    P = n * dx
+    d = np.minimum(np.arange(n) * dx, P - np.arange(n) * dx)
+    G = np.zeros((n, n, n), np.complex128)
+    for i in range(-images, images + 1):
+        for j in range(-images, images + 1):
+            for l in range(-images, images + 1):
+                r = np.sqrt((d[:, None, None] + i * P) ** 2
+                            + (d[None, :, None] + j * P) ** 2
+                            + (d[None, None, :] + l * P) ** 2)
+                G += np.exp(1j * k * r) / (4 * np.pi * np.where(r > 0, r, 1.0))
+    m = _off_axis_mask(d, dx, 3)
+    assert np.abs(x[m] - G[m]).max() / np.abs(G[m]).max() < 1e-3

@@ -160,3 +160,40 @@ def test_slab_with_mixed_boundary_condition():
     # outside the solution decays with the extrapolation length
     ratio = u[xa - 9] / u[xa - 5]
     assert ratio == pytest.approx(np.exp(-4 * dx / ze), rel=0.05)
+
+
+@pytest.mark.parametrize("form", ["antisymmetric", "flux"])
+def test_iterate_follows_the_dense_recurrence(form):
+    """Algorithm 1 in the block forms: x_{i+1} = x_i + alpha B (L+I)^-1 (y - A x_i)
+    (Sec. 2.1), with (L+I)^-1 taken as the dense inverse of L + I rather than
+    the closed form; the history is ||Delta_i|| / ||Delta_1|| at x0 = 0, so its
+    first entry is exactly 1."""
+    shape, dx = (6, 4), 1.0
+    if form == "antisymmetric":
+        k2, S = _gain_medium(shape, 11)
+        cf = ov.antisymmetric_helmholtz(k2, S, dx)
+        op = ov.Antisymmetric(cf)
+    else:
+        eta, D, S = _diffusion_medium(shape, 12)
+        cf = ov.flux_diffusion(eta, D, S, dx)
+        op = ov.Flux(cf)
+    y = cf["y"]
+    full = y.shape
+    L = _dense_from(op.L, full)
+    Vd = _dense_from(op.V, full)
+    Bd = _dense_from(op.B, full)
+    A = L + Vd
+    LpI_inv = np.linalg.inv(L + np.eye(L.shape[0]))
+    alpha, n_iter = 0.7, 9
+    x, hist = ov.iterate(op, y, alpha, n_iter)
+    xd = np.zeros(y.size, np.complex128)
+    ref = np.linalg.norm(Bd @ LpI_inv @ y.ravel())
+    hd = []
+    for _ in range(n_iter):
+        d = Bd @ LpI_inv @ (y.ravel() - A @ xd)
+        xd = xd + alpha * d
+        hd.append(np.linalg.norm(d) / ref)
+    assert hist[0] == pytest.approx(1.0, rel=1e-12)
+    assert np.allclose(hist, hd, rtol=1e-10)
+    assert np.linalg.norm(x.ravel() - xd) / np.linalg.norm(xd) < 1e-11
+    assert ov.reference_norm(op, y) == pytest.approx(ref, rel=1e-12)
