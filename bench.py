@@ -59,7 +59,7 @@ def parse():
                    help="256-point strided-axis transforms on the tensor cores")
     p.add_argument("--no-tma", action="store_true",
                    help="strided-axis passes without TMA staging (comparison)")
-    p.add_argument("--cpu-iters", type=int, default=3)
+    p.add_argument("--cpu-iters", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, plain and roofline legs")
     p.add_argument("--batch", type=int, default=64,
@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--fno-epochs", type=int, default=20)
     p.add_argument("--fno-test", type=int, default=256, help="held-out media")
     p.add_argument("--no-variants", action="store_true", help="skip the block-variant leg")
+    p.add_argument("--no-diffusion", action="store_true",
+                   help="skip the 3-D diffusion leg of the Helmholtz line")
     return p.parse_args()
 
 
@@ -429,6 +431,8 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
                         "iter_per_s": r["iterations"] / dt,
                         "s_to_min_residual": dt * (int(h.argmin()) + 1) / r["iterations"]}
     out["library_comparator"] = cufft_leg(torch, dev, cf, V, y, shape)
+    if args.ndim == 3 and args.workload == "helmholtz" and not args.no_diffusion:
+        out["diffusion3d_%d" % args.n] = diffusion3d_leg(args, torch, dev)
     out["helmholtz2d_128"] = helmholtz2d_leg(args, torch, dev)
     if args.batch > 0:
         out["batched"] = batched_leg(args, torch, dev)
@@ -438,6 +442,68 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
         out["fno_warm_start"] = fno_leg(args, torch, dev)
     if not args.no_variants:
         out["variants"] = variants_leg(args, torch, dev)
+    return out
+
+
+def diffusion3d_leg(args, torch, dev):
+    """The second 3-D workload: steady diffusion on an n^3 grid (log-normal
+    absorption, median 0.01 per px, sigma_log 0.5, smoothed over 6 px; D = 1;
+    centre point source; real V), solved to the bench tolerance the same way
+    as the main line (create + solve + destroy per step, CUDA events, inputs
+    resident: 320 MiB > L2, no flush).  Also: plain FP32 Algorithm 1, and the
+    per-pass roofline on the real-V floor (28 B per point) and on the
+    schedule's bytes."""
+    from paper_2207_14222_gb300 import canon, inputs
+    from paper_2207_14222_gb300.solver import Solver
+    n = args.n
+    cf = canon.canonical(inputs.diffusion_3d(n, seed=0))
+    shape = cf["V"].shape
+    V = torch.from_numpy(cf["V"]).to(dev)
+    y = torch.from_numpy(cf["y"]).to(dev)
+    x = torch.empty_like(y)
+
+    def step(plain=False):
+        with Solver(shape, cf["a"], cf["b"], V, dx=cf["dx"], plain=plain,
+                    schedule=args.schedule) as s:
+            _, r = s.solve(y, x=x, tol=args.tol, maxit=args.maxit)
+        return r
+
+    out = {"workload": "diffusion3d_%d" % n, "grid": list(shape), "tol": args.tol,
+           "V": "float32 (real)", "step": "create + solve to tol + destroy",
+           "l2": "inputs 320 MiB > L2, no flush"}
+    for name, plain in (("chosen", False), ("plain", True)):
+        for _ in range(3):
+            step(plain)
+        torch.cuda.synchronize()
+        reps = max(args.steps, 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rs = [step(plain) for _ in range(reps)]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        r = rs[-1]
+        out[name] = {"s_to_residual": ms / 1e3, "iterations": r["iterations"],
+                     "refinements": r["refinements"], "converged": bool(r["converged"]),
+                     "final_rel_residual": r["final_rel_residual"],
+                     "iter_per_s": sum(q["iterations"] for q in rs) / (reps * ms / 1e3)}
+    with Solver(shape, cf["a"], cf["b"], V, dx=cf["dx"], schedule=args.schedule) as s:
+        s.solve(y, x=x, tol=0.0, maxit=5)
+        passes = s.time_passes(y, x, iters=20)
+    per_it_ms = sum(p["ms"] for p in passes)
+    peak, kind = measured_hbm_peak()
+    dom = max(passes, key=lambda p: p["ms"])
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    out["roofline"] = {
+        "bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+        "unit": "GB/s", "frac": achieved / peak, "peak_source": kind,
+        "iteration_ms": per_it_ms,
+        "iteration_frac": sum(p["bytes"] for p in passes) / (per_it_ms * 1e-3) / 1e9 / peak,
+        "passes": [{"name": p["name"], "ms": round(p["ms"], 5),
+                    "GBps": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)} for p in passes]}
+    out["roofline"].update(schedule_efficiency(passes, int(np.prod(shape)), True, per_it_ms, peak))
+    out["roofline"]["floor_frac"] = (out["roofline"]["floor_bytes_per_point"] * np.prod(shape)
+                                     / (per_it_ms * 1e-3) / 1e9 / peak)
     return out
 
 
@@ -785,44 +851,72 @@ def _oracle_setup(prob):
     return cf, Lh, uo
 
 
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _time_oracle(uo, cf, Lh, alpha, iters, workers, warm=1):
+    """Seconds per iteration of the FP64 oracle's Algorithm 1 (its FFT on
+    ``workers`` host threads), after ``warm`` untimed iterations."""
+    import scipy.fft as sfft
+    with sfft.set_workers(workers):
+        x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, warm, ref_norm=1.0)
+        t0 = time.perf_counter()
+        uo.iterate(cf["V"], cf["y"], Lh, alpha, iters, x0=x, ref_norm=1.0)
+        return (time.perf_counter() - t0) / iters
+
+
 def cpu_baseline(args, prob, iters=None):
-    """The FP64 oracle as it stands, a bounded sample of the same workload."""
+    """The FP64 oracle as it stands, a bounded sample of the same workload:
+    all host cores (its FFT threaded by scipy.fft), and one core beside it."""
     iters = iters or args.cpu_iters
     cf, Lh, uo = _oracle_setup(prob)
     alpha = uo.alpha_star(cf["V"])
-    t0 = time.perf_counter()
-    uo.iterate(cf["V"], cf["y"], Lh, alpha, iters, ref_norm=1.0)
-    dt = time.perf_counter() - t0
-    return {"value": iters / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": "%d iterations of Algorithm 1 on the %s workload, FP64 NumPy "
-                      "(single-threaded FFT), setup untimed" % (iters, workload_name(args))}
+    cores = _host_cores()
+    dt = _time_oracle(uo, cf, Lh, alpha, iters, cores)
+    dt1 = _time_oracle(uo, cf, Lh, alpha, max(2, iters // 5), 1, warm=0)
+    return {"value": 1.0 / dt, "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "sample": "%d timed iterations (after one untimed) of Algorithm 1 on the %s "
+                      "workload, FP64 oracle with its FFT (scipy.fft) on %d host threads; "
+                      "setup untimed" % (iters, workload_name(args), cores),
+            "single_core": {"value": 1.0 / dt1, "unit": "iter/s", "cores": 1,
+                            "sample": "%d timed iterations, one thread"
+                                      % max(2, iters // 5)}}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    import scipy.fft as sfft
     prob = workload(args)
     cf, Lh, uo = _oracle_setup(prob)
     alpha = uo.alpha_star(cf["V"])
+    cores = _host_cores()
     x = np.zeros_like(cf["y"])
-    for _ in range(max(args.warmup, 0)):
-        x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, 1, x0=x, ref_norm=1.0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, 1, x0=x, ref_norm=1.0)
-    dt = time.perf_counter() - t0
+    with sfft.set_workers(cores):
+        for _ in range(max(args.warmup, 0)):
+            x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, 1, x0=x, ref_norm=1.0)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            x, _ = uo.iterate(cf["V"], cf["y"], Lh, alpha, 1, x0=x, ref_norm=1.0)
+        dt = time.perf_counter() - t0
     value = args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "grid": [args.n] * 3, "tol": args.tol,
+        "config": {"workload": workload_name(args),
+                   "grid": [args.n] * args.ndim, "tol": args.tol,
                    "step": "one iteration of the FP64 CPU oracle (bounded sample)"},
-        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d timed iterations of Algorithm 1 (FP64 NumPy oracle) on "
-                                   "the %s workload" % (args.steps, workload_name(args))},
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d timed iterations of Algorithm 1 (FP64 oracle, FFT on "
+                                   "%d host threads) on the %s workload"
+                                   % (args.steps, cores, workload_name(args))},
         "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

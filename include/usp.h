@@ -309,22 +309,32 @@ usp_status usp_canon_diffusion(const double* eta, double D, const double* S,
  * For callers that cannot allocate device memory -- e.g. a process whose
  * device memory was handed to another allocator at start-up, or a hot loop
  * that must not call cudaMalloc/cudaFree because they synchronise the
- * device.  Runs plain Algorithm 1 (no FP64 refinement) from x = 0 on the
- * caller's V, y and x, with all scratch (one field, partial sums, state,
- * residual history) in a fixed area of USP_NOALLOC_BYTES compiled into the
- * library, which every GPU that loads the library keeps until the process
- * exits.  Grids up to USP_NOALLOC_MAX_POINTS points and maxit up to
- * USP_NOALLOC_MAX_ITERS; larger requests return USP_ERR_UNSUPPORTED_SIZE /
- * USP_ERR_INVALID_ARG with a message (usp_last_error).  It calls no
- * allocation routine.
+ * device.  Runs the plain fixed-point iteration of this library (FP32, no
+ * FP64 refinement), starting from x = 0, on the caller's V, y and x, with
+ * all scratch (one field, partial sums, state, residual history) in a fixed
+ * area of USP_NOALLOC_BYTES compiled into the library.  Grids: each axis a
+ * power of two in [2, 256], at most USP_NOALLOC_MAX_POINTS points in all;
+ * quadratic symbol only (USP_LSYM_QUADRATIC); maxit up to
+ * USP_NOALLOC_MAX_ITERS.  Other axis lengths (96, 192, 384, 512) and larger
+ * grids return USP_ERR_UNSUPPORTED_SIZE, a tabulated symbol or a larger
+ * maxit USP_ERR_INVALID_ARG, each with a message (usp_last_error).  It calls
+ * no allocation routine.
  *
- * The first call on a device does a one-time set-up there (looks up the
- * scratch area's device address, uploads the FFT twiddle tables): make that
- * first call before any stream capture.  All calls share the one scratch
- * area, whose contents persist between calls (each call rewrites what must
- * start from zero); calls whose GPU work overlaps in time race on it, so
- * serialise them.  Arguments as for usp_solver_create and usp_solve (device
- * pointers V, y, x; x is output only).  Synchronous. */
+ * The scratch area belongs to the library's device code, which CUDA may
+ * load lazily: the area may then be reserved on a device only at the first
+ * call there, not when the library is loaded.  A caller that hands its
+ * device memory to another allocator should therefore make one call first
+ * (a tiny grid will do); if the reservation fails, the call returns
+ * USP_ERR_OOM.  Once reserved, the area stays with the device until the
+ * process exits.
+ *
+ * The first call on a device also does a one-time set-up there (looks up
+ * the scratch area's device address, uploads the FFT twiddle tables): make
+ * that first call before any stream capture.  All calls share the one
+ * scratch area, whose contents persist between calls (each call rewrites
+ * what must start from zero); calls whose GPU work overlaps in time race on
+ * it, so serialise them.  Other arguments as for usp_solver_create and
+ * usp_solve (device pointers V, y, x; x is output only).  Synchronous. */
 #define USP_NOALLOC_MAX_POINTS (1 << 19)
 #define USP_NOALLOC_MAX_ITERS 65536
 #define USP_NOALLOC_BYTES 4751872

@@ -21,12 +21,16 @@ What it computes (paper Sec. 2 and 2.1):
     of Delta evaluations.  Norms are the plain discrete l2 norm, summed in
     FP64.
 
-The FFT is a library primitive (numpy.fft) standing in for the transform's
+The FFT is a library primitive (scipy.fft) standing in for the transform's
 definition; ``oracle.dft`` holds the definition itself and the tests pin one
-against the other.
+against the other.  scipy.fft runs on as many host threads as the caller
+allows (``scipy.fft.set_workers``); the arithmetic does not depend on it.
+Inputs are taken to complex128 before every transform (scipy.fft would
+otherwise keep single precision for complex64 data).
 """
 
 import numpy as np
+import scipy.fft as sfft
 
 
 # ----------------------------------------------------------------- symbol ---
@@ -51,12 +55,12 @@ def lhat(shape, dx, a, b):
 
 def apply_L_plus_I_inverse(t, Lhat):
     """(L+I)^-1 t = F^-1 [ F t / (L^ + 1) ]  (Eq. laplacian_inverse)."""
-    return np.fft.ifftn(np.fft.fftn(t) / (Lhat + 1.0))
+    return sfft.ifftn(sfft.fftn(np.asarray(t, np.complex128)) / (Lhat + 1.0))
 
 
 def apply_L(x, Lhat):
     """L x = F^-1 [ L^ F x ]."""
-    return np.fft.ifftn(Lhat * np.fft.fftn(x))
+    return sfft.ifftn(Lhat * sfft.fftn(np.asarray(x, np.complex128)))
 
 
 def apply_A(x, V, Lhat):

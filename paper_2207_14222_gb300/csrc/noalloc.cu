@@ -1,5 +1,5 @@
-// noalloc.cu -- usp_solve_noalloc: plain Algorithm 1 for callers that cannot
-// allocate device memory.
+// noalloc.cu -- usp_solve_noalloc: the plain FP32 fixed-point iteration for
+// callers that cannot allocate device memory.
 //
 // Who needs this: a caller whose process has handed (nearly) all device
 // memory to another allocator up front, or whose hot loop must not call
@@ -8,8 +8,10 @@
 // library create a solver, which allocates its scratch field, reduction
 // buffers and state.  This entry point instead works inside one fixed
 // scratch area compiled into the library: a file-scope __device__ array of
-// USP_NOALLOC_BYTES bytes (see usp.h), which every GPU that loads the library
-// holds until the process exits.
+// USP_NOALLOC_BYTES bytes (see usp.h).  CUDA may load the library's device
+// code lazily, so the array may be reserved on a device only at the first
+// call there (the symbol lookup loads the module); a failed reservation
+// returns USP_ERR_OOM.  Once reserved, it stays until the process exits.
 //
 // The array's name is only a host-side stand-in in host code; its device
 // address comes from cudaGetSymbolAddress, looked up once per device (with
@@ -67,7 +69,7 @@ usp_status scratch_base(unsigned char** out) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       set_last_error("usp_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return USP_ERR_CUDA;
+      return e == cudaErrorMemoryAllocation ? USP_ERR_OOM : USP_ERR_CUDA;
     }
     e = init_twiddles();
     if (e != cudaSuccess) {

@@ -209,6 +209,46 @@ def test_parity_full_size_256_bench_configuration(torch_cuda):
     _check_trajectory(torch_cuda, shape, prob, 3)
 
 
+def test_parity_full_size_256_diffusion(torch_cuda):
+    """The second full-size workload (3-D steady diffusion 256^3, Sec. 3.2 in
+    its scalar form: real float32 V through the staged rows and strided-axis
+    passes), automatic schedule, every output compared with the oracle after
+    4 iterations."""
+    shape = (256, 256, 256)
+    prob = inputs.diffusion_3d(256, seed=0)
+    _check_trajectory(torch_cuda, shape, prob, 4, vreal=True)
+
+
+@pytest.mark.parametrize("workload", ["helmholtz", "diffusion"])
+def test_full_size_256_solve_reaches_tolerance(torch_cuda, workload):
+    """The benchmark's solve at 256^3 (FP32 iteration with FP64 refinement,
+    automatic schedule) to 1e-6: the oracle's own preconditioned residual of
+    the returned field (one FP64 evaluation of Algorithm 1's Delta) is below
+    1.5e-6 of the oracle's reference norm, and the reported reference norm
+    matches the oracle's."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (256, 256, 256)
+    if workload == "helmholtz":
+        cf, V, y = _prep(inputs.helmholtz_3d(256, seed=0))
+    else:
+        cf, V, y = _prep(inputs.diffusion_3d(256, seed=0), vreal=True)
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), dx=cf["dx"]) as s:
+        x, res = s.solve(torch.from_numpy(y).to(dev), tol=1e-6, maxit=20000,
+                         allow_not_converged=False)
+        torch.cuda.synchronize()
+        xg = x.cpu().numpy().astype(np.complex128)
+    del x
+    assert res["converged"] == 1 and res["final_rel_residual"] < 1e-6
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    V64, y64 = V.astype(np.complex128), y.astype(np.complex128)
+    ref = uo.reference_norm(y64, V64, Lh)
+    assert res["ref_norm"] == pytest.approx(ref, rel=1e-5)
+    d = uo.residual_delta(xg, y64, V64, Lh)
+    assert np.linalg.norm(d) / ref < 1.5e-6
+
+
 # The TF32 three-product split rounds each 16-point stage at about twice
 # FP32's error, so the raw trajectory gets 5e-5; the path's bar (1e-5 to the
 # oracle) applies after refinement, in the converged-solve test below.

@@ -66,11 +66,23 @@ def test_dft_shift_theorem():
 
 @pytest.mark.parametrize("shape", [(16,), (6, 10), (4, 6, 8)])
 def test_library_fft_matches_definition(shape):
-    """The oracle's FFT step (a library primitive) against the definition."""
+    """The oracle's FFT step (a library primitive, scipy.fft, here also on
+    several threads and from complex64 input) against the definition."""
+    import scipy.fft as sfft
     x = _rand(shape, 4)
-    assert np.allclose(np.fft.fftn(x), dft.naive_dftn(x), atol=1e-11)
-    assert np.allclose(np.fft.ifftn(x), dft.naive_dftn(x, inverse=True),
+    assert np.allclose(sfft.fftn(x), dft.naive_dftn(x), atol=1e-11)
+    assert np.allclose(sfft.ifftn(x), dft.naive_dftn(x, inverse=True),
                        atol=1e-12)
+    with sfft.set_workers(4):
+        assert np.allclose(sfft.fftn(x), dft.naive_dftn(x), atol=1e-11)
+    # the operators transform in FP64 whatever the input precision
+    x32 = x.astype(np.complex64)
+    Lh = np.full(shape, 0.5 + 0.25j)
+    got = uo.apply_L_plus_I_inverse(x32, Lh)
+    expect = dft.naive_dftn(dft.naive_dftn(x32.astype(np.complex128)) / (Lh + 1.0),
+                            inverse=True)
+    assert got.dtype == np.complex128
+    assert np.allclose(got, expect, atol=1e-13)
 
 
 # ------------------------------------------------------------- the symbol ---

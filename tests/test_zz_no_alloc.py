@@ -56,7 +56,8 @@ def _noalloc(torch, shape, cf, Vd, yd, xd, tol, maxit, alpha=0.0):
     return st, res
 
 
-@pytest.mark.parametrize("shape, vreal", [((32, 32, 32), False), ((64, 128), True)])
+@pytest.mark.parametrize("shape, vreal", [((32, 32, 32), False), ((64, 128), True),
+                                          ((256,), True), ((16, 32, 64), True)])
 def test_noalloc_matches_regular_solver_twice(torch_cuda, shape, vreal):
     torch = torch_cuda
     from paper_2207_14222_gb300.solver import Solver
