@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--ndim", type=int, default=3, choices=[2, 3],
                    help="2: the 2-D n x n Helmholtz medium (sigma 4 px, ABL n/8) instead of the 3-D one")
     p.add_argument("--workload", default="helmholtz", choices=["helmholtz", "diffusion"])
+    p.add_argument("--nz", type=int, default=0,
+                   help="3-D slab nz x n x n instead of n^3 (small profiling cases)")
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--maxit", type=int, default=20000)
     p.add_argument("--schedule", type=int, default=0)
@@ -103,12 +105,22 @@ def workload(args, seed=0):
         if args.workload == "helmholtz":
             return inputs.helmholtz_2d(args.n, seed=seed, abl_width=max(4, args.n // 8))
         return inputs.random_diffusion((args.n, args.n), seed, sigma_px=4.0)
+    if args.nz:
+        # profiling slabs: nz x n x n, the same medium statistics
+        shape = (args.nz, args.n, args.n)
+        if args.workload == "helmholtz":
+            return inputs.random_helmholtz(shape, seed, sigma_px=6.0 * args.n / 256,
+                                           amplitude=0.3, abl_width=max(2, args.nz // 8))
+        return inputs.random_diffusion(shape, seed, sigma_px=6.0 * args.n / 256,
+                                       median_eta=0.01)
     if args.workload == "helmholtz":
         return inputs.helmholtz_3d(args.n, seed=seed)
     return inputs.diffusion_3d(args.n, seed=seed)
 
 
 def workload_name(args):
+    if args.nz:
+        return "%s3d_%dx%dx%d" % (args.workload, args.nz, args.n, args.n)
     return "%s%dd_%d" % (args.workload, args.ndim, args.n)
 
 
@@ -341,7 +353,7 @@ def run_ours(args):
                 "grid": list(shape),
                 "tol": args.tol,
                 "mode": "plain" if args.plain else "fp32+fp64-refinement",
-                "schedule": ["auto", "pencil", "fused", "on-chip"][args.schedule],
+                "schedule": ["auto", "pencil", "fused", "on-chip", "split"][args.schedule],
                 "tma": not args.no_tma,
                 "cols_tile": args.cols_tile or "default",
                 "tc_dft": args.tc_dft,

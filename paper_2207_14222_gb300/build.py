@@ -33,6 +33,7 @@ SOURCES = [
     "variant_api.cpp",
     "tc_kernels.cu",
     "onchip_kernels.cu",
+    "split3d_kernels.cu",
 ]
 
 

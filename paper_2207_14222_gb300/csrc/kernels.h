@@ -247,6 +247,45 @@ cudaError_t rows_tma_init();
 int rows_tma_tile_rows(int n);
 cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s);
 
+// Split-y two-pass schedule (split3d_kernels.cu), grids nz x 256 x 256 with
+// nz in {32, 64, 128, 256}: the rows pass does the x transform and the
+// 32-point y1 stage of each tile (plane z, rows y = 8 y1 + y2); the column
+// pass the 8-point y2 stage, the z transform and the spectral multiply.
+// Scratch layout S[k1][xb][z][((y2 ^ (z & 3)) << 2) | xi], kx = 4 xb + xi.
+enum SplitMode : int {
+  SPLIT_PRE = 0,    // t = (1-V) x + y ; forward x and y1 stages      (phase prologue)
+  SPLIT_FULL = 1,   // inverse y1, x ; Delta, update, norm ; next t ; forward x, y1
+  SPLIT_POST = 2    // inverse y1, x ; Delta, norm (reference pass: no update)
+};
+struct SplitArgs {
+  int flags;            // F_XZERO, F_REF, F_VREAL
+  int nz;
+  const float2* x_in;
+  float2* x_out;
+  const float2* y;      // bulk-copied rows: 16-byte aligned
+  const void* V;        // bulk-copied rows: 16-byte aligned
+  float2* buf;          // scratch in the split layout
+  const float2* tw;     // W_256^m table (device)
+  double* partials;     // one double per CTA
+  DevState* st;
+  double* hist;
+  float alpha;
+};
+struct SplitColsArgs {
+  int flags;            // F_REVERSE
+  float2* buf;          // scratch in the split layout (16-byte aligned)
+  const float2* tw;     // W_256^m table (device)
+  DevState* st;
+  Sym<float> sym;       // quadratic symbol or table (k-space C order)
+};
+cudaError_t split_init();
+bool split_nz_ok(int nz);
+int split_cols_ctas_per_sm(int nz);
+// map: the scratch viewed as 5-D {xi 4, y2 8, z nz, xb 64, k1 32}, box {4, 1, 1, 64, 32}.
+cudaError_t launch_split_rows(int mode, const CUtensorMap& map, const SplitArgs& a, int grid,
+                              cudaStream_t s);
+cudaError_t launch_split_cols(int nz, const SplitColsArgs& a, int grid, cudaStream_t s);
+
 // Launchers (pencil_kernels.cu).  n = transform length (power of two, 2..256).
 cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaStream_t s);
 cudaError_t launch_rows_f64(int n, const RowsArgs<double>& a, int64_t grid, cudaStream_t s);

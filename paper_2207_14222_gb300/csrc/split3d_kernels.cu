@@ -1,0 +1,621 @@
+// split3d_kernels.cu -- the split-y two-pass schedule of one fixed-point
+// iteration (Algorithm 1 with the forward-eliminated operator of Sec. 2.1;
+// (L+I)^-1 = F^-1 diag(1/(Lhat+1)) F, Eq. laplacian_inverse) for grids
+// nz x 256 x 256, nz a power of two in [32, 256].
+//
+// The y transform (length 256) is split as y = 8 y1 + y2, k = k1 + 32 k2:
+//   Y[k1 + 32 k2] = sum_y2 W_8^(y2 k2) [ W_256^(y2 k1) sum_y1 t[8 y1 + y2] W_32^(y1 k1) ].
+// The inner 32-point transform over y1 needs only the 32 rows {8 y1 + y2}
+// of one plane, so the rows pass does it beside the x transform; the outer
+// 8-point transform over y2 joins the z transform in the column pass.
+// Neither pass needs a whole plane on chip, and no CTA waits for another:
+//
+//   rows pass (tile = plane z and residue y2: 32 rows of 256 values):
+//       inverse y1 stage, inverse FFT x, Delta = (1-V)(u - x), x += alpha Delta,
+//       ||Delta||^2, t = (1-V) x + y, FFT x, forward y1 stage
+//   column pass (tile = k1 and 4 consecutive kx, over all y2 and z):
+//       y2 stage, FFT z, x 1/(N (Lhat + 1)), inverse FFT z, inverse y2 stage
+//
+// Algorithmic HBM bytes per point and iteration: rows 48 (read scratch, x, V,
+// y; write x, scratch; 44 with a real V) + columns 16 = 64, against 96 for the
+// pencil schedule.
+//
+// Scratch layout (complex64), chosen so that a column tile is one contiguous
+// block and the rows pass reads and writes whole 32-byte sectors:
+//   S[k1][xb][z][slot],  kx = 4 xb + xi,  slot = ((y2 ^ (z & 3)) << 2) | xi,
+// 32 values (256 bytes) per (k1, xb, z).  The XOR puts the y2 groups of
+// neighbouring z rows on different shared-memory banks in the column pass.
+//
+// Both kernels are persistent and stage their tiles with the copy engine
+// (bulk copies and one 5-D tensor load); every wait is bounded and a wait that
+// gives up marks the solve ST_TIMEOUT after the copies in flight have landed.
+#include "fft_core.cuh"
+#include "iteration_state.cuh"
+#include "kernels.h"
+#include "tma.cuh"
+
+namespace usp {
+
+namespace {
+
+constexpr int SP_N = 256;           // nx = ny
+constexpr int SP_R1 = 32;           // y1 points (rows pass)
+constexpr int SP_R2 = 8;            // y2 points (column pass)
+constexpr int SP_XB = 4;            // kx per column tile
+constexpr int SP_ROW = SP_R2 * SP_XB;   // values per (k1, xb, z)
+constexpr int SA_THREADS = 512;
+constexpr int SA_TILE = SP_R1 * SP_N;   // values per rows tile
+constexpr uint32_t SA_TILE_BYTES = SA_TILE * sizeof(float2);
+constexpr int SC_TILES = SP_R1 * (SP_N / SP_XB);   // column tiles (k1, xb)
+
+// 5-D tiled TMA load global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 1-D bulk copy shared -> global (this thread's bulk async-group).
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+
+// The 256-point transform of one row held by 16 threads (g), exchanging
+// through the row's own 256 values in shared memory (XOR-swizzled rows).
+template <bool INV>
+__device__ __forceinline__ void fft_row256(float2* v, float2* exr, const float2* tws, int g) {
+  constexpr int N1 = 16, N2 = 16;
+  stage1<256, INV>(v, g, tws);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) exr[k1 * N2 + (g ^ k1)] = v[k1];
+  __syncthreads();
+  float2 w[N1];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) w[n2] = exr[g * N2 + (n2 ^ g)];
+  __syncthreads();
+  stage2<256, INV>(w);
+#pragma unroll
+  for (int q = 0; q < N1; ++q) v[q] = w[q];
+}
+
+// The strided-axis transform of the column pass: 32 columns (lane) of
+// length N, G threads each; exchange rows k1 N2 + (n2 ^ (k1 mod N2)).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_col32(float2* v, float2* ex, const float2* tws, int g, int lane) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
+  stage1<N, INV>(v, g, tws);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + (g ^ (k1 & (N2 - 1)))) * 32 + lane] = v[k1];
+  __syncthreads();
+  float2 w[N1];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int k1 = g + G * s;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + (n2 ^ (k1 & (N2 - 1)))) * 32 + lane];
+  }
+  __syncthreads();
+  stage2<N, INV>(w);
+#pragma unroll
+  for (int q = 0; q < N1; ++q) v[q] = w[q];
+}
+
+__device__ __forceinline__ float axis_p2(const Sym<float>& s, int ax, int k) {
+  const float p = s.ks[ax] * float(signed_freq(k, s.n[ax]));
+  return p * p;
+}
+
+// Stage-1 twiddle table of the M-point transform from the W_256^e table.
+template <int M>
+__device__ __forceinline__ void load_stage1_twiddles(float2* dst, const float2* w256) {
+  for (int m = threadIdx.x; m < M; m += blockDim.x)
+    dst[m] = w256[stage1_twiddle_exponent(m, Split<M>::N2) * (256 / M)];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ rows pass ---
+//
+// One 512-thread CTA per SM walks tiles u = (z, y2) (u = 8 z + y2) with three
+// 64 KB shared-memory slots:
+//   SU: the tile's scratch values [k1][kx] (one 5-D tensor load); exchange of
+//       the inverse transforms, then refilled with the next tile's values;
+//   SV: V rows [y1][x] (32 bulk copies); refilled after the pointwise step;
+//   SY: y rows [y1][x] (32 bulk copies); exchange of the forward transforms,
+//       refilled once the forward y1 stage has read it.
+// Thread roles: rows (f = tid / 16 is the row y1, g = tid % 16 its line
+// thread) for the x transform and the pointwise step; columns (kx = tid / 2,
+// h = tid % 2) for the y1 stage, where the pair (kx, 0), (kx, 1) splits the
+// 32-point transform into two 16-point ones (even and odd rows) and one
+// radix-2 step exchanged by a lane shuffle.
+template <int MODE>
+__global__ void __launch_bounds__(SA_THREADS, 1)
+    k_split_rows(const __grid_constant__ CUtensorMap smap, const SplitArgs a) {
+  constexpr bool POST = MODE != SPLIT_PRE;   // the tile starts from the scratch (inverse part)
+  constexpr bool PRE = MODE != SPLIT_POST;   // the tile ends with t = B x + y and its transform
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* SU = reinterpret_cast<float2*>(smem_raw);
+  float2* SV = SU + SA_TILE;
+  float2* SY = SV + SA_TILE;
+  float2* w256 = SY + SA_TILE;     // W_256^e
+  float2* tws = w256 + SP_N;       // stage-1 twiddles of the 256-point row transform
+  __shared__ __align__(8) uint64_t bars[3];
+  __shared__ double red[SA_THREADS / 32];
+  __shared__ int is_last, ok_flag;
+
+  if (a.st->done) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int f = tid >> 4, g = tid & 15;     // row roles
+  const int kx = tid >> 1, h = tid & 1;     // column roles
+  const bool xzero = (a.flags & F_XZERO) != 0;
+  const bool vreal = (a.flags & F_VREAL) != 0;
+  const bool ref = (a.flags & F_REF) != 0;
+  const bool need_x = !xzero;
+  const int64_t tiles = (int64_t)a.nz * SP_R2;
+  const int64_t t0 = blockIdx.x, stride = gridDim.x;
+  const int64_t my = t0 < tiles ? (tiles - t0 + stride - 1) / stride : 0;
+  bool ok = true;
+  // thread 0 counts, per slot, the loads issued and the phases it saw
+  // complete, so that a failed wait can let the copies in flight land
+  int64_t n_issued[3] = {0, 0, 0}, n_waited[3] = {0, 0, 0};
+
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  for (int m = tid; m < SP_N; m += SA_THREADS) w256[m] = a.tw[m];
+  load_stage1_twiddles<256>(tws, a.tw);
+  __syncthreads();
+
+  auto tile_of = [&](int64_t k) { return t0 + k * stride; };
+  // global row (z * 256 + y) of row y1 of tile u
+  auto row_of = [&](int64_t u, int y1) { return (u >> 3) * SP_N + SP_R2 * y1 + (u & 7); };
+  // warp 0: issue the copies of slot `which` for the k-th tile
+  auto issue = [&](int which, int64_t k) {
+    const int64_t u = tile_of(k);
+    if (lane == 0) ++n_issued[which];
+    if (which == 0) {
+      if (lane == 0) {
+        const int z = int(u >> 3), y2 = int(u & 7);
+        mbar_arrive_expect_tx(&bars[0], SA_TILE_BYTES);
+        tma_load_5d(SU, &smap, 0, y2 ^ (z & 3), z, 0, 0, &bars[0]);
+      }
+      return;
+    }
+    const bool real = which == 1 && vreal;
+    const uint32_t rb = real ? SP_N * 4u : SP_N * 8u;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[which], SP_R1 * rb);
+    __syncwarp();
+    const int64_t r = row_of(u, lane);
+    const char* src = which == 1 ? reinterpret_cast<const char*>(a.V) + r * rb
+                                 : reinterpret_cast<const char*>(a.y + r * SP_N);
+    char* dst = reinterpret_cast<char*>(which == 1 ? SV : SY) + lane * rb;
+    bulk_load(dst, src, rb, &bars[which]);
+  };
+  auto wait_bar = [&](int i, uint32_t parity) {
+    if (tid == 0) {
+      ok_flag = mbar_wait(&bars[i], parity) ? 1 : 0;
+      n_waited[i] += ok_flag;
+    }
+    __syncthreads();
+    ok = ok && ok_flag;
+  };
+  auto release_then = [&](int which, int64_t k) {   // slot free -> refill for tile k
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid < 32 && k < my) issue(which, k);
+  };
+  float2 xr[16];
+  auto prefetch_x = [&](int64_t k) {   // this thread's x at points g + 16 q of its row
+    const int64_t row = row_of(tile_of(k), f);
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      xr[q] = need_x ? a.x_in[row * SP_N + g + 16 * q] : make_float2(0.f, 0.f);
+  };
+
+  if (tid < 32 && my > 0) {
+    if (POST) issue(0, 0);
+    issue(1, 0);
+    if (PRE) issue(2, 0);
+  }
+  if (my > 0) prefetch_x(0);
+
+  float acc = 0.f;
+  for (int64_t k = 0; k < my && ok; ++k) {
+    const uint32_t par = uint32_t(k & 1);
+    const int64_t u = tile_of(k);
+    const int z = int(u >> 3), y2 = int(u & 7);
+    const int64_t row = row_of(u, f);
+    float2 v[16];
+    if (POST) {
+      wait_bar(0, par);
+      if (!ok) break;
+      // inverse y1 stage: thread (kx, h) takes k1 = kk + 16 h
+      float2 c[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const int k1 = kk + 16 * h;
+        c[kk] = cmulc(SU[k1 * SP_N + kx], w256[(y2 * k1) & 255]);   // undo W_256^(y2 k1)
+      }
+      // undo the radix-2 step: (kx,0) holds X[kk], (kx,1) X[kk+16]
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float2 r;
+        r.x = __shfl_xor_sync(0xffffffffu, c[kk].x, 1);
+        r.y = __shfl_xor_sync(0xffffffffu, c[kk].y, 1);
+        // h = 0: X[kk] + X[kk+16]; h = 1: (X[kk] - X[kk+16]) conj(W_32^kk)
+        const float sg = h ? -1.f : 1.f;
+        const float2 t = make_float2(fmaf(sg, c[kk].x, r.x), fmaf(sg, c[kk].y, r.y));
+        c[kk] = h ? cmulc(t, w256[8 * kk]) : t;
+      }
+      DFT<16, true, float2>::run(c);   // rows y1 = 2 i + h
+      __syncthreads();                 // SU read by all
+#pragma unroll
+      for (int i = 0; i < 16; ++i) SU[(2 * i + h) * SP_N + kx] = c[i];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = SU[f * SP_N + 16 * q + g];
+      __syncthreads();
+      fft_row256<true>(v, SU + f * SP_N, tws, g);   // u at x = g + 16 q
+      release_then(0, k + 1);
+      wait_bar(1, par);
+      if (PRE) wait_bar(2, par);
+      if (!ok) break;
+      // Delta = (1-V)(u - x); x += alpha Delta; next t = (1-V) x + y
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int cidx = f * SP_N + g + 16 * q;
+        const float2 vv = vreal ? make_float2(reinterpret_cast<const float*>(SV)[cidx], 0.f) : SV[cidx];
+        const float br = 1.f - vv.x, bi = -vv.y;
+        const float ur = v[q].x - xr[q].x, ui = v[q].y - xr[q].y;
+        const float dr = br * ur - bi * ui, di = br * ui + bi * ur;
+        acc += dr * dr + di * di;
+        const float2 xn = make_float2(xr[q].x + a.alpha * dr, xr[q].y + a.alpha * di);
+        if (!ref) a.x_out[row * SP_N + g + 16 * q] = xn;
+        if (PRE) {
+          const float2 yv = SY[cidx];
+          v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
+        }
+      }
+      release_then(1, k + 1);
+      // with POST the next x is read at the end of this tile: the inverse
+      // part of the next tile covers its latency
+      if (!PRE && k + 1 < my) prefetch_x(k + 1);
+    } else {
+      wait_bar(1, par);
+      wait_bar(2, par);
+      if (!ok) break;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int cidx = f * SP_N + g + 16 * q;
+        const float2 vv = vreal ? make_float2(reinterpret_cast<const float*>(SV)[cidx], 0.f) : SV[cidx];
+        const float br = 1.f - vv.x, bi = -vv.y;
+        const float2 yv = SY[cidx];
+        v[q] = make_float2(yv.x + br * xr[q].x - bi * xr[q].y, yv.y + br * xr[q].y + bi * xr[q].x);
+      }
+      release_then(1, k + 1);
+      if (k + 1 < my) prefetch_x(k + 1);
+    }
+    if (PRE) {
+      // forward FFT x (positions g + 16 q in -> frequencies g + 16 q out)
+      float2 tmp[16];
+      out_to_in<256>(v, tmp);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = tmp[q];
+      fft_row256<false>(v, SY + f * SP_N, tws, g);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) SY[f * SP_N + g + 16 * q] = v[q];
+      __syncthreads();
+      // forward y1 stage: thread (kx, h) takes rows 2 i + h
+      float2 c[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) c[i] = SY[(2 * i + h) * SP_N + kx];
+      release_then(2, k + 1);
+      DFT<16, false, float2>::run(c);   // h = 0: E[kk]; h = 1: O[kk]
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const float2 o = h ? cmul(c[kk], w256[8 * kk]) : c[kk];   // W_32^kk O[kk]
+        float2 r;
+        r.x = __shfl_xor_sync(0xffffffffu, o.x, 1);
+        r.y = __shfl_xor_sync(0xffffffffu, o.y, 1);
+        // h = 0: X[kk] = E + W O; h = 1: X[kk+16] = E - W O
+        const float sg = h ? -1.f : 1.f;
+        const float2 X = make_float2(fmaf(sg, o.x, r.x), fmaf(sg, o.y, r.y));
+        const int k1 = kk + 16 * h;
+        const int64_t gi = ((int64_t)(k1 * (SP_N / SP_XB) + (kx >> 2)) * a.nz + z) * SP_ROW +
+                           (((y2 ^ (z & 3)) << 2) | (kx & 3));
+        a.buf[gi] = cmul(X, w256[(y2 * k1) & 255]);
+      }
+      if (POST && k + 1 < my) prefetch_x(k + 1);
+    }
+  }
+
+  if (!ok && tid == 0) {
+    // let the copies still in flight land before the CTA's shared memory goes
+    for (int i = 0; i < 3; ++i)
+      for (int64_t p = n_waited[i]; p < n_issued[i]; ++p) mbar_wait(&bars[i], uint32_t(p & 1));
+    a.st->status = ST_TIMEOUT;
+    a.st->done = 1;
+  }
+  // ||Delta||^2: block partial, the last block finalises (fixed order)
+  if (!POST) return;
+  double dv = (double)acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dv += __shfl_down_sync(0xffffffffu, dv, o);
+  if (lane == 0) red[tid >> 5] = dv;
+  __syncthreads();
+  if (tid == 0) {
+    double bs = 0.0;
+    for (int i = 0; i < SA_THREADS / 32; ++i) bs += red[i];
+    a.partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned tk = atomicAdd(&a.st->ticket, 1u);
+    is_last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    double sm = 0.0;
+    for (unsigned i = tid; i < gridDim.x; i += SA_THREADS) sm += __ldcg(a.partials + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sm += __shfl_down_sync(0xffffffffu, sm, o);
+    __syncthreads();
+    if (lane == 0) red[tid >> 5] = sm;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < SA_THREADS / 32; ++i) tot += red[i];
+      if (a.st->status != ST_TIMEOUT) finalize_iteration(a.st, a.hist, tot, a.flags);
+      a.st->ticket = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------- column pass ---
+//
+// Tiles (k1, xb): the contiguous block S[k1][xb][*][*] of nz x 32 values,
+// moved by 1-D bulk copies through a ring of three slots (two loads in
+// flight while one tile is transformed in its slot).  In the slot, thread
+// roles change twice: (z, xi) pairs for the 8-point y2 stage, then columns
+// c = 4 k2 + xi (lane) with G threads each for the z transform; the values
+// move between the two through the slot itself, laid out [z][c ^ 4 (z & 7)].
+template <int NZ>
+struct SplitCols {
+  static constexpr int G = Split<NZ>::G, N1 = Split<NZ>::N1;
+  static constexpr int THREADS = 32 * G;
+  static constexpr int MINB = 512 / THREADS;
+  static constexpr int TILE = NZ * SP_ROW;
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(float2);
+  static constexpr int PAIRS = NZ * SP_XB / THREADS;   // (z, xi) pairs per thread
+  static constexpr int ZSTEP = THREADS / SP_XB;
+  static constexpr int SLOTS = 3;
+  static_assert(PAIRS >= 1 && PAIRS * THREADS == NZ * SP_XB, "column tile shape");
+};
+
+template <int NZ>
+__global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
+    k_split_cols(const SplitColsArgs a) {
+  typedef SplitCols<NZ> C;
+  constexpr int N1 = C::N1, TILE = C::TILE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* slots = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = slots + C::SLOTS * TILE;   // stage-1 twiddles of the z transform
+  __shared__ __align__(8) uint64_t full[C::SLOTS];
+  __shared__ int ok_flag;
+
+  if (a.st->done) return;
+  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+  const int xi = tid & 3, zb = tid >> 2;
+  const int64_t t0 = blockIdx.x, stride = gridDim.x;
+  const int64_t my = t0 < SC_TILES ? (SC_TILES - t0 + stride - 1) / stride : 0;
+  load_stage1_twiddles<NZ>(tws, a.tw);
+  if (tid == 0) {
+    for (int s = 0; s < C::SLOTS; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const Sym<float> sy = a.sym;
+  const float b1 = sy.b_re + 1.f;
+  float pz2[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) pz2[q] = axis_p2(sy, 0, out_index<NZ>(g, q));
+
+  // walk backwards from the last tile when F_REVERSE (the rows pass wrote the
+  // last k1 blocks last only partly; the order is a tuning choice)
+  const bool rev = (a.flags & F_REVERSE) != 0;
+  auto tile_of = [&](int64_t kk) { return rev ? SC_TILES - 1 - (t0 + kk * stride) : t0 + kk * stride; };
+  auto issue = [&](int64_t kk) {   // thread 0: tile kk into slot kk % SLOTS
+    const int sl = int(kk % C::SLOTS);
+    mbar_arrive_expect_tx(&full[sl], C::TILE_BYTES);
+    bulk_load(slots + sl * TILE, a.buf + tile_of(kk) * TILE, C::TILE_BYTES, &full[sl]);
+  };
+  int64_t ik = 0;
+  if (tid == 0)
+    for (; ik < 2 && ik < my; ++ik) issue(ik);
+
+  int64_t k = 0;
+  bool failed = false;
+  for (; k < my; ++k) {
+    const int s = int(k % C::SLOTS);
+    if (tid == 0) ok_flag = mbar_wait(&full[s], uint32_t((k / C::SLOTS) & 1)) ? 1 : 0;
+    __syncthreads();
+    if (!ok_flag) {
+      failed = true;
+      break;
+    }
+    float2* T = slots + s * TILE;
+    const int64_t t = tile_of(k);
+    const int k1 = int(t >> 6), xb = int(t & 63);
+
+    // forward y2 stage on the (z, xi) pairs
+    float2 w[C::PAIRS][SP_R2];
+#pragma unroll
+    for (int p = 0; p < C::PAIRS; ++p) {
+      const int z = zb + p * C::ZSTEP;
+#pragma unroll
+      for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = T[z * SP_ROW + (((y2 ^ (z & 3)) << 2) | xi)];
+      DFT<SP_R2, false, float2>::run(w[p]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < C::PAIRS; ++p) {
+      const int z = zb + p * C::ZSTEP;
+#pragma unroll
+      for (int k2 = 0; k2 < SP_R2; ++k2) T[z * SP_ROW + ((4 * k2 + xi) ^ (4 * (z & 7)))] = w[p][k2];
+    }
+    __syncthreads();
+    // z transform of column lane = 4 k2 + xi
+    float2 v[N1];
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int zz = in_index<NZ>(g, q);
+      v[q] = T[zz * SP_ROW + (lane ^ (4 * (zz & 7)))];
+    }
+    __syncthreads();
+    fft_col32<NZ, false>(v, T, tws, g, lane);
+    {
+      const int kxx = SP_XB * xb + (lane & 3), ky = k1 + SP_R1 * (lane >> 2);
+      const float p2in = axis_p2(sy, 2, kxx) + axis_p2(sy, 1, ky);
+      if (sy.table) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+          const float2 l = sy.table[((int64_t)out_index<NZ>(g, q) * SP_N + ky) * SP_N + kxx];
+          const float dr = l.x + 1.f;
+          const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, l.y * l.y));
+          v[q] = cmul(v[q], make_float2(dr * sc, -l.y * sc));
+        }
+      } else {
+        // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+          const float p2 = p2in + pz2[q];
+          const float dr = fmaf(sy.a_re, p2, b1);
+          const float di = fmaf(sy.a_im, p2, sy.b_im);
+          const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, di * di));
+          v[q] = cmul(v[q], make_float2(dr * sc, -di * sc));
+        }
+      }
+      float2 tmp[N1];
+      out_to_in<NZ>(v, tmp);
+#pragma unroll
+      for (int q = 0; q < N1; ++q) v[q] = tmp[q];
+    }
+    fft_col32<NZ, true>(v, T, tws, g, lane);
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int zz = out_index<NZ>(g, q);
+      T[zz * SP_ROW + (lane ^ (4 * (zz & 7)))] = v[q];
+    }
+    __syncthreads();
+    // inverse y2 stage
+#pragma unroll
+    for (int p = 0; p < C::PAIRS; ++p) {
+      const int z = zb + p * C::ZSTEP;
+#pragma unroll
+      for (int k2 = 0; k2 < SP_R2; ++k2) w[p][k2] = T[z * SP_ROW + ((4 * k2 + xi) ^ (4 * (z & 7)))];
+      DFT<SP_R2, true, float2>::run(w[p]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < C::PAIRS; ++p) {
+      const int z = zb + p * C::ZSTEP;
+#pragma unroll
+      for (int y2 = 0; y2 < SP_R2; ++y2) T[z * SP_ROW + (((y2 ^ (z & 3)) << 2) | xi)] = w[p][y2];
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_store(a.buf + t * TILE, T, C::TILE_BYTES);
+      bulk_commit();
+      if (ik < my) {
+        // the slot of tile k+2 held tile k-1, whose store was committed one
+        // tile ago: wait until at most the newest group still reads
+        bulk_wait_read<1>();
+        issue(ik);
+        ++ik;
+      }
+    }
+  }
+  if (tid == 0) {
+    bulk_wait<0>();
+    if (failed) {
+      for (int64_t p = k; p < ik; ++p) mbar_wait(&full[p % C::SLOTS], uint32_t((p / C::SLOTS) & 1));
+      a.st->status = ST_TIMEOUT;
+      a.st->done = 1;
+    }
+  }
+}
+
+// ----------------------------------------------------------- launchers ---
+
+static size_t split_rows_smem() { return sizeof(float2) * (3 * SA_TILE + 2 * SP_N); }
+template <int NZ>
+static size_t split_cols_smem() {
+  return sizeof(float2) * (SplitCols<NZ>::SLOTS * SplitCols<NZ>::TILE + NZ);
+}
+
+template <int NZ>
+static cudaError_t split_cols_attr() {
+  return cudaFuncSetAttribute(k_split_cols<NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)split_cols_smem<NZ>());
+}
+
+cudaError_t split_init() {
+  cudaError_t e;
+  const int sm = (int)split_rows_smem();
+  if ((e = cudaFuncSetAttribute(k_split_rows<SPLIT_PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_split_rows<SPLIT_FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_split_rows<SPLIT_POST>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  if ((e = split_cols_attr<32>()) != cudaSuccess) return e;
+  if ((e = split_cols_attr<64>()) != cudaSuccess) return e;
+  if ((e = split_cols_attr<128>()) != cudaSuccess) return e;
+  return split_cols_attr<256>();
+}
+
+bool split_nz_ok(int nz) { return nz == 32 || nz == 64 || nz == 128 || nz == 256; }
+
+int split_cols_ctas_per_sm(int nz) {
+  switch (nz) {
+    case 32: return SplitCols<32>::MINB;
+    case 64: return SplitCols<64>::MINB;
+    case 128: return SplitCols<128>::MINB;
+    case 256: return SplitCols<256>::MINB;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_split_rows(int mode, const CUtensorMap& map, const SplitArgs& a, int grid,
+                              cudaStream_t s) {
+  const size_t sm = split_rows_smem();
+  switch (mode) {
+    case SPLIT_PRE: k_split_rows<SPLIT_PRE><<<grid, SA_THREADS, sm, s>>>(map, a); break;
+    case SPLIT_FULL: k_split_rows<SPLIT_FULL><<<grid, SA_THREADS, sm, s>>>(map, a); break;
+    case SPLIT_POST: k_split_rows<SPLIT_POST><<<grid, SA_THREADS, sm, s>>>(map, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int NZ>
+static cudaError_t split_cols_go(const SplitColsArgs& a, int grid, cudaStream_t s) {
+  k_split_cols<NZ><<<grid, SplitCols<NZ>::THREADS, split_cols_smem<NZ>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_cols(int nz, const SplitColsArgs& a, int grid, cudaStream_t s) {
+  switch (nz) {
+    case 32: return split_cols_go<32>(a, grid, s);
+    case 64: return split_cols_go<64>(a, grid, s);
+    case 128: return split_cols_go<128>(a, grid, s);
+    case 256: return split_cols_go<256>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace usp

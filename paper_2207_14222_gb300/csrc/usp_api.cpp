@@ -77,6 +77,7 @@ static usp_status ensure_device_init() {
   CUDA_TRY(plane_kernel_init());
   CUDA_TRY(cols_tma_init());
   CUDA_TRY(rows_tma_init());
+  CUDA_TRY(split_init());
   CUDA_TRY(tc_cols_init());
   if (dev < 64) g_init_mask |= (1ull << dev);
   return USP_OK;
@@ -140,6 +141,8 @@ struct usp_solver {
   int num_sms = 0;
   bool maps_ok = false;            // TMA tensor maps of the scratch field
   CUtensorMap map_ax[3][2];        // [tile 32 / 16 / 8 columns][axis]: strided-axis views of s->buf
+  bool split_ok = false;           // split_map encoded (grids nz x 256 x 256)
+  CUtensorMap split_map;           // the scratch in the split layout, 5-D (rows-pass tiles)
 };
 
 // Column-tile width of the staged strided-axis passes when the options leave
@@ -188,7 +191,24 @@ static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, in
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The scratch in the split-y layout S[k1][xb][z][slot] viewed as 5-D
+// {xi 4, y2 8, z nz, xb 64, k1 32} (8-byte elements); a rows-pass tile (plane
+// z, residue y2) is the box {4, 1, 1, 64, 32}.
+static bool encode_split_map(CUtensorMap* m, void* base, int nz) {
+  if (!tensor_map_encoder()) return false;
+  const cuuint64_t dims[5] = {4, 8, (cuuint64_t)nz, 64, 32};
+  const cuuint64_t strides[4] = {32, 256, (cuuint64_t)nz * 256, (cuuint64_t)nz * 256 * 64};
+  const cuuint32_t box[5] = {4, 1, 1, 64, 32};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 5, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static void build_maps(usp_solver* s) {
+  s->split_ok = s->B == 1 && s->ndim == 3 && split_nz_ok(s->n[0]) && s->n[1] == 256 &&
+                s->n[2] == 256 && encode_split_map(&s->split_map, s->buf, s->n[0]);
   s->maps_ok = false;
   if (s->ndim < 2) return;
   bool ok = true;
@@ -538,14 +558,80 @@ static std::vector<PassLaunch> fused_passes(usp_solver* s, const float2* y, cons
   return P;
 }
 
+// ---- split-y two-pass schedule (grids nz x 256 x 256, split3d_kernels.cu)
+
+static bool split_supported(const usp_solver* s) { return s->split_ok && s->num_sms > 0; }
+// Schedule 4 selects it; the rows pass bulk-copies rows of y and V and the
+// column pass whole tiles of the scratch, so all three must be 16-byte
+// aligned (otherwise the pencil schedule runs).
+static bool use_split(const usp_solver* s, const float2* y) {
+  if (!split_supported(s) || s->opt.schedule != 4) return false;
+  return (((uintptr_t)y | (uintptr_t)s->V | (uintptr_t)s->buf) & 15u) == 0;
+}
+
+static SplitArgs split_args(usp_solver* s, const float2* y, const float2* xin, float2* xout,
+                            int flags) {
+  SplitArgs a{};
+  a.flags = flags | (s->vreal ? F_VREAL : 0);
+  a.nz = s->n[0];
+  a.x_in = xin;
+  a.x_out = xout;
+  a.y = y;
+  a.V = s->V;
+  a.buf = s->buf;
+  a.tw = s->tw32;
+  a.partials = s->partials;
+  a.st = s->st;
+  a.hist = s->hist;
+  a.alpha = (float)s->alpha;
+  return a;
+}
+
+static std::function<cudaError_t(cudaStream_t)> split_rows_pass(usp_solver* s, int mode,
+                                                                const SplitArgs& a) {
+  const int grid = (int)std::min<int64_t>((int64_t)s->n[0] * 8, s->num_sms);
+  const CUtensorMap map = s->split_map;
+  return [=](cudaStream_t t) { return launch_split_rows(mode, map, a, grid, t); };
+}
+
+static std::vector<PassLaunch> split_prologue(usp_solver* s, const float2* y, const float2* xin,
+                                              int flags) {
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0;
+  SplitArgs a = split_args(s, y, xin, nullptr, flags & ~F_REF);
+  return {{"split_rows_pre", 16.0 + (xz ? 0.0 : 8.0 + vb), split_rows_pass(s, SPLIT_PRE, a)}};
+}
+
+static std::vector<PassLaunch> split_passes(usp_solver* s, const float2* y, const float2* xin,
+                                            float2* xout, int flags) {
+  std::vector<PassLaunch> P;
+  const double vb = s->vreal ? 4.0 : 8.0;
+  const bool xz = (flags & F_XZERO) != 0, ref = (flags & F_REF) != 0;
+  SplitColsArgs c{};
+  c.flags = 0;
+  c.buf = s->buf;
+  c.tw = s->tw32;
+  c.st = s->st;
+  c.sym = s->symf;
+  const int nz = s->n[0];
+  const int cgrid = s->num_sms * split_cols_ctas_per_sm(nz);
+  P.push_back({"split_cols", 16.0, [=](cudaStream_t t) { return launch_split_cols(nz, c, cgrid, t); }});
+  SplitArgs a = split_args(s, y, xin, xout, flags);
+  if (ref) P.push_back({"split_rows_post", 8.0 + vb, split_rows_pass(s, SPLIT_POST, a)});
+  else P.push_back({"split_rows_full", 32.0 + vb + (xz ? 0.0 : 8.0), split_rows_pass(s, SPLIT_FULL, a)});
+  return P;
+}
+
 static std::vector<PassLaunch> iteration_passes(usp_solver* s, const float2* y, const float2* xin,
                                                 float2* xout, int flags) {
+  if (use_split(s, y)) return split_passes(s, y, xin, xout, flags);
   if (use_fused(s, y)) return fused_passes(s, y, xin, xout, flags);
   return pencil_passes(s, y, xin, xout, flags);
 }
 
 static std::vector<PassLaunch> prologue_passes(usp_solver* s, const float2* y, const float2* xin,
                                                int flags) {
+  if (use_split(s, y)) return split_prologue(s, y, xin, flags);
   if (use_fused(s, y)) return fused_prologue(s, y, xin, flags);
   return pencil_prologue(s, y, xin, flags);
 }
@@ -867,10 +953,13 @@ extern "C" usp_status usp_solver_set_options(usp_solver* s, const usp_options* o
   if (!s || !opt) return fail(USP_ERR_INVALID_ARG, "NULL argument");
   if (opt->cols_tile != 0 && opt->cols_tile != 8 && opt->cols_tile != 16 && opt->cols_tile != 32)
     return fail(USP_ERR_INVALID_ARG, "cols_tile must be 0, 8, 16 or 32");
-  if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 3)
+  if (opt->chunk < 0 || opt->max_refinements < 0 || opt->schedule < 0 || opt->schedule > 4)
     return fail(USP_ERR_INVALID_ARG, "invalid option value");
   if (opt->schedule == 2 && !fused_supported(s))
     return fail(USP_ERR_UNSUPPORTED_SIZE, "the fused schedule needs a 3-D grid nz x 256 x 256");
+  if (opt->schedule == 4 && !split_supported(s))
+    return fail(USP_ERR_UNSUPPORTED_SIZE,
+                "the split schedule needs one 3-D problem on a grid nz x 256 x 256, nz in {32, 64, 128, 256}");
   if (opt->onchip_rows != 0 && opt->onchip_rows != 8 && opt->onchip_rows != 16)
     return fail(USP_ERR_INVALID_ARG, "onchip_rows must be 0, 8 or 16");
   if (opt->schedule == 3 && !onchip_available(s, onchip_rows_of(s, *opt)))

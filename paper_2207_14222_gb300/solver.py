@@ -35,7 +35,8 @@ class Solver:
     plain : True runs Algorithm 1 exactly (no FP64 refinement).
     schedule : 0 auto, 1 pencil passes, 2 fused two-pass 3-D schedule,
             3 on-chip (square 2-D grids of side 32, 64, 96, 128, 192, 256:
-            the fields stay in one thread-block cluster's shared memory).
+            the fields stay in one thread-block cluster's shared memory),
+            4 split-y two-pass 3-D schedule (nz x 256 x 256, nz in 32..256).
     no_tma : True loads the strided-axis passes with plain global accesses.
     cols_tile : columns per staged strided-axis tile (8, 16, 32; 0 default).
     tc_dft : True runs the 256-point strided-axis transforms on the tensor cores.
