@@ -123,9 +123,10 @@ typedef struct {
    *    cluster and one launch runs a whole phase of iterations;
    * 4: split-y schedule (single 3-D problems nz x 256 x 256, nz in {32, 64,
    *    128, 256}): two passes per iteration; the 256-point y transform is
-   *    split 32 x 8 between a rows pass (x transform and 32-point stage,
-   *    tiles of 32 rows of one plane) and a column pass (8-point stage, z
-   *    transform, spectral multiply); 64 bytes per point per iteration.    */
+   *    split 16 x 16 between a rows pass (x transform and one 16-point
+   *    stage, tiles of 16 rows of one plane) and a column pass (the other
+   *    16-point stage, z transform, spectral multiply); 64 bytes per point
+   *    per iteration.                                                       */
   int32_t schedule;
   /* iterations per CUDA-graph launch between convergence polls; 0: auto   */
   int32_t chunk;

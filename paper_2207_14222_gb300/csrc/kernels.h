@@ -249,9 +249,9 @@ cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t 
 
 // Split-y two-pass schedule (split3d_kernels.cu), grids nz x 256 x 256 with
 // nz in {32, 64, 128, 256}: the rows pass does the x transform and the
-// 32-point y1 stage of each tile (plane z, rows y = 8 y1 + y2); the column
-// pass the 8-point y2 stage, the z transform and the spectral multiply.
-// Scratch layout S[k1][xb][z][((y2 ^ (z & 3)) << 2) | xi], kx = 4 xb + xi.
+// 16-point y1 stage of each tile (plane z, rows y = 16 y1 + y2); the column
+// pass the 16-point y2 stage, the z transform and the spectral multiply.
+// Scratch layout S[k1][xb][z][((y2 ^ (z & 7)) << 1) | xi], kx = 2 xb + xi.
 enum SplitMode : int {
   SPLIT_PRE = 0,    // t = (1-V) x + y ; forward x and y1 stages      (phase prologue)
   SPLIT_FULL = 1,   // inverse y1, x ; Delta, update, norm ; next t ; forward x, y1
@@ -281,7 +281,7 @@ struct SplitColsArgs {
 cudaError_t split_init();
 bool split_nz_ok(int nz);
 int split_cols_ctas_per_sm(int nz);
-// map: the scratch viewed as 5-D {xi 4, y2 8, z nz, xb 64, k1 32}, box {4, 1, 1, 64, 32}.
+// map: the scratch viewed as 5-D {xi 2, y2 16, z nz, xb 128, k1 16}, box {2, 1, 1, 128, 16}.
 cudaError_t launch_split_rows(int mode, const CUtensorMap& map, const SplitArgs& a, int grid,
                               cudaStream_t s);
 cudaError_t launch_split_cols(int nz, const SplitColsArgs& a, int grid, cudaStream_t s);

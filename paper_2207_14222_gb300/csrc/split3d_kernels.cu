@@ -3,17 +3,17 @@
 // (L+I)^-1 = F^-1 diag(1/(Lhat+1)) F, Eq. laplacian_inverse) for grids
 // nz x 256 x 256, nz a power of two in [32, 256].
 //
-// The y transform (length 256) is split as y = 8 y1 + y2, k = k1 + 32 k2:
-//   Y[k1 + 32 k2] = sum_y2 W_8^(y2 k2) [ W_256^(y2 k1) sum_y1 t[8 y1 + y2] W_32^(y1 k1) ].
-// The inner 32-point transform over y1 needs only the 32 rows {8 y1 + y2}
+// The y transform (length 256) is split as y = 16 y1 + y2, k = k1 + 16 k2:
+//   Y[k1 + 16 k2] = sum_y2 W_16^(y2 k2) [ W_256^(y2 k1) sum_y1 t[16 y1 + y2] W_16^(y1 k1) ].
+// The inner 16-point transform over y1 needs only the 16 rows {16 y1 + y2}
 // of one plane, so the rows pass does it beside the x transform; the outer
-// 8-point transform over y2 joins the z transform in the column pass.
+// 16-point transform over y2 joins the z transform in the column pass.
 // Neither pass needs a whole plane on chip, and no CTA waits for another:
 //
-//   rows pass (tile = plane z and residue y2: 32 rows of 256 values):
+//   rows pass (tile = plane z and residue y2: 16 rows of 256 values):
 //       inverse y1 stage, inverse FFT x, Delta = (1-V)(u - x), x += alpha Delta,
 //       ||Delta||^2, t = (1-V) x + y, FFT x, forward y1 stage
-//   column pass (tile = k1 and 4 consecutive kx, over all y2 and z):
+//   column pass (tile = k1 and 2 consecutive kx, over all y2 and z):
 //       y2 stage, FFT z, x 1/(N (Lhat + 1)), inverse FFT z, inverse y2 stage
 //
 // Algorithmic HBM bytes per point and iteration: rows 48 (read scratch, x, V,
@@ -21,9 +21,10 @@
 // pencil schedule.
 //
 // Scratch layout (complex64), chosen so that a column tile is one contiguous
-// block and the rows pass reads and writes whole 32-byte sectors:
-//   S[k1][xb][z][slot],  kx = 4 xb + xi,  slot = ((y2 ^ (z & 3)) << 2) | xi,
-// 32 values (256 bytes) per (k1, xb, z).  The XOR puts the y2 groups of
+// block:
+//   S[k1][xb][z][slot],  kx = 2 xb + xi,  slot = ((y2 ^ (z & 7)) << 1) | xi,
+// 32 values (256 bytes) per (k1, xb, z).  The rows pass reads and writes it in
+// 16-byte pieces (the two kx of a column tile); the XOR puts the y2 groups of
 // neighbouring z rows on different shared-memory banks in the column pass.
 //
 // Both kernels are persistent and stage their tiles with the copy engine
@@ -39,14 +40,15 @@ namespace usp {
 namespace {
 
 constexpr int SP_N = 256;           // nx = ny
-constexpr int SP_R1 = 32;           // y1 points (rows pass)
-constexpr int SP_R2 = 8;            // y2 points (column pass)
-constexpr int SP_XB = 4;            // kx per column tile
+constexpr int SP_R1 = 16;           // y1 points (rows pass)
+constexpr int SP_R2 = 16;           // y2 points (column pass)
+constexpr int SP_XB = 2;            // kx per column tile
+constexpr int SP_NXB = SP_N / SP_XB;
 constexpr int SP_ROW = SP_R2 * SP_XB;   // values per (k1, xb, z)
-constexpr int SA_THREADS = 512;
+constexpr int SA_THREADS = 256;         // 16 rows x 16 line threads = 256 kx
 constexpr int SA_TILE = SP_R1 * SP_N;   // values per rows tile
 constexpr uint32_t SA_TILE_BYTES = SA_TILE * sizeof(float2);
-constexpr int SC_TILES = SP_R1 * (SP_N / SP_XB);   // column tiles (k1, xb)
+constexpr int SC_TILES = SP_R1 * SP_NXB;   // column tiles (k1, xb)
 
 // 5-D tiled TMA load global -> shared, completing on an mbarrier.
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -65,41 +67,27 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
                : "memory");
 }
 
-// The 256-point transform of one row held by 16 threads (g), exchanging
-// through the row's own 256 values in shared memory (XOR-swizzled rows).
-template <bool INV>
-__device__ __forceinline__ void fft_row256(float2* v, float2* exr, const float2* tws, int g) {
-  constexpr int N1 = 16, N2 = 16;
-  stage1<256, INV>(v, g, tws);
-#pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) exr[k1 * N2 + (g ^ k1)] = v[k1];
-  __syncthreads();
-  float2 w[N1];
-#pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) w[n2] = exr[g * N2 + (n2 ^ g)];
-  __syncthreads();
-  stage2<256, INV>(w);
-#pragma unroll
-  for (int q = 0; q < N1; ++q) v[q] = w[q];
-}
-
-// The strided-axis transform of the column pass: 32 columns (lane) of
-// length N, G threads each; exchange rows k1 N2 + (n2 ^ (k1 mod N2)).
+// The N-point transform of one line held by the G = Split<N>::G threads g of
+// one warp (a row of the rows pass, a column of the column pass), exchanging
+// through the line's own N values in shared memory: exchange row k1 holds
+// position n2 at k1 N2 + (n2 ^ (k1 mod N2)).  The line's threads share a
+// warp, so a warp barrier orders the exchange; the caller's warp must not
+// touch another warp's line between its own last access and this call.
 template <int N, bool INV>
-__device__ __forceinline__ void fft_col32(float2* v, float2* ex, const float2* tws, int g, int lane) {
+__device__ __forceinline__ void fft_line(float2* v, float2* exl, const float2* tws, int g) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = Split<N>::G, S = Split<N>::S;
   stage1<N, INV>(v, g, tws);
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[(k1 * N2 + (g ^ (k1 & (N2 - 1)))) * 32 + lane] = v[k1];
-  __syncthreads();
+  for (int k1 = 0; k1 < N1; ++k1) exl[k1 * N2 + (g ^ (k1 & (N2 - 1)))] = v[k1];
+  __syncwarp();
   float2 w[N1];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int k1 = g + G * s;
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = ex[(k1 * N2 + (n2 ^ (k1 & (N2 - 1)))) * 32 + lane];
+    for (int n2 = 0; n2 < N2; ++n2) w[s * N2 + n2] = exl[k1 * N2 + (n2 ^ (k1 & (N2 - 1)))];
   }
-  __syncthreads();
+  __syncwarp();
   stage2<N, INV>(w);
 #pragma unroll
   for (int q = 0; q < N1; ++q) v[q] = w[q];
@@ -121,20 +109,18 @@ __device__ __forceinline__ void load_stage1_twiddles(float2* dst, const float2* 
 
 // ------------------------------------------------------------ rows pass ---
 //
-// One 512-thread CTA per SM walks tiles u = (z, y2) (u = 8 z + y2) with three
-// 64 KB shared-memory slots:
+// Two 256-thread CTAs per SM walk tiles u = (z, y2) (u = 16 z + y2), each
+// with three 32 KB shared-memory slots:
 //   SU: the tile's scratch values [k1][kx] (one 5-D tensor load); exchange of
 //       the inverse transforms, then refilled with the next tile's values;
-//   SV: V rows [y1][x] (32 bulk copies); refilled after the pointwise step;
-//   SY: y rows [y1][x] (32 bulk copies); exchange of the forward transforms,
+//   SV: V rows [y1][x] (16 bulk copies); refilled after the pointwise step;
+//   SY: y rows [y1][x] (16 bulk copies); exchange of the forward transforms,
 //       refilled once the forward y1 stage has read it.
 // Thread roles: rows (f = tid / 16 is the row y1, g = tid % 16 its line
-// thread) for the x transform and the pointwise step; columns (kx = tid / 2,
-// h = tid % 2) for the y1 stage, where the pair (kx, 0), (kx, 1) splits the
-// 32-point transform into two 16-point ones (even and odd rows) and one
-// radix-2 step exchanged by a lane shuffle.
+// thread) for the x transform and the pointwise step; columns (kx = tid) for
+// the y1 stage, a 16-point transform in registers.
 template <int MODE>
-__global__ void __launch_bounds__(SA_THREADS, 1)
+__global__ void __launch_bounds__(SA_THREADS, 2)
     k_split_rows(const __grid_constant__ CUtensorMap smap, const SplitArgs a) {
   constexpr bool POST = MODE != SPLIT_PRE;   // the tile starts from the scratch (inverse part)
   constexpr bool PRE = MODE != SPLIT_POST;   // the tile ends with t = B x + y and its transform
@@ -151,7 +137,7 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
   if (a.st->done) return;
   const int tid = threadIdx.x, lane = tid & 31;
   const int f = tid >> 4, g = tid & 15;     // row roles
-  const int kx = tid >> 1, h = tid & 1;     // column roles
+  const int kx = tid;                       // column role
   const bool xzero = (a.flags & F_XZERO) != 0;
   const bool vreal = (a.flags & F_VREAL) != 0;
   const bool ref = (a.flags & F_REF) != 0;
@@ -174,16 +160,17 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
 
   auto tile_of = [&](int64_t k) { return t0 + k * stride; };
   // global row (z * 256 + y) of row y1 of tile u
-  auto row_of = [&](int64_t u, int y1) { return (u >> 3) * SP_N + SP_R2 * y1 + (u & 7); };
-  // warp 0: issue the copies of slot `which` for the k-th tile
+  auto row_of = [&](int64_t u, int y1) { return (u >> 4) * SP_N + SP_R2 * y1 + (u & 15); };
+  // warp 0: issue the copies of slot `which` for the k-th tile (lanes < 16
+  // each copy one row of V or y)
   auto issue = [&](int which, int64_t k) {
     const int64_t u = tile_of(k);
     if (lane == 0) ++n_issued[which];
     if (which == 0) {
       if (lane == 0) {
-        const int z = int(u >> 3), y2 = int(u & 7);
+        const int z = int(u >> 4), y2 = int(u & 15);
         mbar_arrive_expect_tx(&bars[0], SA_TILE_BYTES);
-        tma_load_5d(SU, &smap, 0, y2 ^ (z & 3), z, 0, 0, &bars[0]);
+        tma_load_5d(SU, &smap, 0, y2 ^ (z & 7), z, 0, 0, &bars[0]);
       }
       return;
     }
@@ -191,16 +178,31 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
     const uint32_t rb = real ? SP_N * 4u : SP_N * 8u;
     if (lane == 0) mbar_arrive_expect_tx(&bars[which], SP_R1 * rb);
     __syncwarp();
-    const int64_t r = row_of(u, lane);
-    const char* src = which == 1 ? reinterpret_cast<const char*>(a.V) + r * rb
-                                 : reinterpret_cast<const char*>(a.y + r * SP_N);
-    char* dst = reinterpret_cast<char*>(which == 1 ? SV : SY) + lane * rb;
-    bulk_load(dst, src, rb, &bars[which]);
+    if (lane < SP_R1) {
+      const int64_t r = row_of(u, lane);
+      const char* src = which == 1 ? reinterpret_cast<const char*>(a.V) + r * rb
+                                   : reinterpret_cast<const char*>(a.y + r * SP_N);
+      char* dst = reinterpret_cast<char*>(which == 1 ? SV : SY) + lane * rb;
+      bulk_load(dst, src, rb, &bars[which]);
+    }
   };
   auto wait_bar = [&](int i, uint32_t parity) {
     if (tid == 0) {
       ok_flag = mbar_wait(&bars[i], parity) ? 1 : 0;
       n_waited[i] += ok_flag;
+    }
+    __syncthreads();
+    ok = ok && ok_flag;
+  };
+  // the V slot, and with last == 2 the y slot too, behind one block barrier
+  auto wait_bars = [&](int last, uint32_t parity) {
+    if (tid == 0) {
+      int good = 1;
+      for (int i = 1; i <= last && good; ++i) {
+        good = mbar_wait(&bars[i], parity) ? 1 : 0;
+        n_waited[i] += good;
+      }
+      ok_flag = good;
     }
     __syncthreads();
     ok = ok && ok_flag;
@@ -229,42 +231,27 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
   for (int64_t k = 0; k < my && ok; ++k) {
     const uint32_t par = uint32_t(k & 1);
     const int64_t u = tile_of(k);
-    const int z = int(u >> 3), y2 = int(u & 7);
+    const int z = int(u >> 4), y2 = int(u & 15);
     const int64_t row = row_of(u, f);
     float2 v[16];
     if (POST) {
       wait_bar(0, par);
       if (!ok) break;
-      // inverse y1 stage: thread (kx, h) takes k1 = kk + 16 h
+      // inverse y1 stage: undo W_256^(y2 k1), inverse 16-point DFT over k1
       float2 c[16];
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const int k1 = kk + 16 * h;
-        c[kk] = cmulc(SU[k1 * SP_N + kx], w256[(y2 * k1) & 255]);   // undo W_256^(y2 k1)
-      }
-      // undo the radix-2 step: (kx,0) holds X[kk], (kx,1) X[kk+16]
-#pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        float2 r;
-        r.x = __shfl_xor_sync(0xffffffffu, c[kk].x, 1);
-        r.y = __shfl_xor_sync(0xffffffffu, c[kk].y, 1);
-        // h = 0: X[kk] + X[kk+16]; h = 1: (X[kk] - X[kk+16]) conj(W_32^kk)
-        const float sg = h ? -1.f : 1.f;
-        const float2 t = make_float2(fmaf(sg, c[kk].x, r.x), fmaf(sg, c[kk].y, r.y));
-        c[kk] = h ? cmulc(t, w256[8 * kk]) : t;
-      }
-      DFT<16, true, float2>::run(c);   // rows y1 = 2 i + h
+      for (int k1 = 0; k1 < 16; ++k1) c[k1] = cmulc(SU[k1 * SP_N + kx], w256[(y2 * k1) & 255]);
+      DFT<16, true, float2>::run(c);   // rows y1
       __syncthreads();                 // SU read by all
 #pragma unroll
-      for (int i = 0; i < 16; ++i) SU[(2 * i + h) * SP_N + kx] = c[i];
+      for (int i = 0; i < 16; ++i) SU[i * SP_N + kx] = c[i];
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = SU[f * SP_N + 16 * q + g];
-      __syncthreads();
-      fft_row256<true>(v, SU + f * SP_N, tws, g);   // u at x = g + 16 q
+      __syncwarp();   // row f (this warp's) is read before its exchange reuses it
+      fft_line<256, true>(v, SU + f * SP_N, tws, g);   // u at x = g + 16 q
       release_then(0, k + 1);
-      wait_bar(1, par);
-      if (PRE) wait_bar(2, par);
+      wait_bars(PRE ? 2 : 1, par);
       if (!ok) break;
       // Delta = (1-V)(u - x); x += alpha Delta; next t = (1-V) x + y
 #pragma unroll
@@ -287,8 +274,7 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
       // part of the next tile covers its latency
       if (!PRE && k + 1 < my) prefetch_x(k + 1);
     } else {
-      wait_bar(1, par);
-      wait_bar(2, par);
+      wait_bars(2, par);
       if (!ok) break;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
@@ -307,30 +293,20 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
       out_to_in<256>(v, tmp);
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = tmp[q];
-      fft_row256<false>(v, SY + f * SP_N, tws, g);
+      fft_line<256, false>(v, SY + f * SP_N, tws, g);
 #pragma unroll
       for (int q = 0; q < 16; ++q) SY[f * SP_N + g + 16 * q] = v[q];
       __syncthreads();
-      // forward y1 stage: thread (kx, h) takes rows 2 i + h
+      // forward y1 stage: 16-point DFT over the rows, then W_256^(y2 k1)
       float2 c[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) c[i] = SY[(2 * i + h) * SP_N + kx];
+      for (int i = 0; i < 16; ++i) c[i] = SY[i * SP_N + kx];
       release_then(2, k + 1);
-      DFT<16, false, float2>::run(c);   // h = 0: E[kk]; h = 1: O[kk]
+      DFT<16, false, float2>::run(c);
+      float2* dst = a.buf + ((int64_t)(kx >> 1) * a.nz + z) * SP_ROW + (((y2 ^ (z & 7)) << 1) | (kx & 1));
+      const int64_t k1_stride = (int64_t)SP_NXB * a.nz * SP_ROW;
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const float2 o = h ? cmul(c[kk], w256[8 * kk]) : c[kk];   // W_32^kk O[kk]
-        float2 r;
-        r.x = __shfl_xor_sync(0xffffffffu, o.x, 1);
-        r.y = __shfl_xor_sync(0xffffffffu, o.y, 1);
-        // h = 0: X[kk] = E + W O; h = 1: X[kk+16] = E - W O
-        const float sg = h ? -1.f : 1.f;
-        const float2 X = make_float2(fmaf(sg, o.x, r.x), fmaf(sg, o.y, r.y));
-        const int k1 = kk + 16 * h;
-        const int64_t gi = ((int64_t)(k1 * (SP_N / SP_XB) + (kx >> 2)) * a.nz + z) * SP_ROW +
-                           (((y2 ^ (z & 3)) << 2) | (kx & 3));
-        a.buf[gi] = cmul(X, w256[(y2 * k1) & 255]);
-      }
+      for (int k1 = 0; k1 < 16; ++k1) dst[k1 * k1_stride] = cmul(c[k1], w256[(y2 * k1) & 255]);
       if (POST && k + 1 < my) prefetch_x(k + 1);
     }
   }
@@ -381,9 +357,13 @@ __global__ void __launch_bounds__(SA_THREADS, 1)
 // Tiles (k1, xb): the contiguous block S[k1][xb][*][*] of nz x 32 values,
 // moved by 1-D bulk copies through a ring of three slots (two loads in
 // flight while one tile is transformed in its slot).  In the slot, thread
-// roles change twice: (z, xi) pairs for the 8-point y2 stage, then columns
-// c = 4 k2 + xi (lane) with G threads each for the z transform; the values
-// move between the two through the slot itself, laid out [z][c ^ 4 (z & 7)].
+// roles change twice: (z, xi) pairs for the 16-point y2 stage, then columns
+// c = 2 k2 + xi, each held by the G threads of one warp, for the z
+// transform.  The values move between the two through the slot itself,
+// column-major: column c at c nz, position z ^ (8 (c & 1)) (the XOR puts
+// the even and odd columns of one y2-stage store on different banks).  The
+// z transform's exchange then stays inside each column, so only the two
+// transposes need block barriers.
 template <int NZ>
 struct SplitCols {
   static constexpr int G = Split<NZ>::G, N1 = Split<NZ>::N1;
@@ -391,17 +371,24 @@ struct SplitCols {
   static constexpr int MINB = 512 / THREADS;
   static constexpr int TILE = NZ * SP_ROW;
   static constexpr uint32_t TILE_BYTES = TILE * sizeof(float2);
-  static constexpr int PAIRS = NZ * SP_XB / THREADS;   // (z, xi) pairs per thread
+  // (z, xi) pairs per thread in the y2 stage (threads beyond the pairs idle)
+  static constexpr int PAIRS = (NZ * SP_XB + THREADS - 1) / THREADS;
   static constexpr int ZSTEP = THREADS / SP_XB;
   static constexpr int SLOTS = 3;
-  static_assert(PAIRS >= 1 && PAIRS * THREADS == NZ * SP_XB, "column tile shape");
+  static_assert(NZ >= 16, "column swizzle needs 16-value blocks");
 };
+
+// Position of z in column c of the column-major view of a slot.
+template <int NZ>
+__device__ __forceinline__ int colpos(int c, int z) {
+  return c * NZ + (z ^ (8 * (c & 1)));
+}
 
 template <int NZ>
 __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     k_split_cols(const SplitColsArgs a) {
   typedef SplitCols<NZ> C;
-  constexpr int N1 = C::N1, TILE = C::TILE;
+  constexpr int N1 = C::N1, TILE = C::TILE, G = C::G;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* slots = reinterpret_cast<float2*>(smem_raw);
   float2* tws = slots + C::SLOTS * TILE;   // stage-1 twiddles of the z transform
@@ -409,8 +396,9 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
   __shared__ int ok_flag;
 
   if (a.st->done) return;
-  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-  const int xi = tid & 3, zb = tid >> 2;
+  const int tid = threadIdx.x;
+  const int c = tid / G, g = tid % G;      // z-transform roles: column c = 2 k2 + xi
+  const int xi = tid & 1, zb = tid >> 1;   // y2-stage roles
   const int64_t t0 = blockIdx.x, stride = gridDim.x;
   const int64_t my = t0 < SC_TILES ? (SC_TILES - t0 + stride - 1) / stride : 0;
   load_stage1_twiddles<NZ>(tws, a.tw);
@@ -426,8 +414,6 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
 #pragma unroll
   for (int q = 0; q < N1; ++q) pz2[q] = axis_p2(sy, 0, out_index<NZ>(g, q));
 
-  // walk backwards from the last tile when F_REVERSE (the rows pass wrote the
-  // last k1 blocks last only partly; the order is a tuning choice)
   const bool rev = (a.flags & F_REVERSE) != 0;
   auto tile_of = [&](int64_t kk) { return rev ? SC_TILES - 1 - (t0 + kk * stride) : t0 + kk * stride; };
   auto issue = [&](int64_t kk) {   // thread 0: tile kk into slot kk % SLOTS
@@ -451,36 +437,37 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     }
     float2* T = slots + s * TILE;
     const int64_t t = tile_of(k);
-    const int k1 = int(t >> 6), xb = int(t & 63);
+    const int k1 = int(t / SP_NXB), xb = int(t % SP_NXB);
 
     // forward y2 stage on the (z, xi) pairs
     float2 w[C::PAIRS][SP_R2];
 #pragma unroll
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
+      if (z < NZ) {
 #pragma unroll
-      for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = T[z * SP_ROW + (((y2 ^ (z & 3)) << 2) | xi)];
-      DFT<SP_R2, false, float2>::run(w[p]);
+        for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = T[z * SP_ROW + (((y2 ^ (z & 7)) << 1) | xi)];
+        DFT<SP_R2, false, float2>::run(w[p]);
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
+      if (z < NZ) {
 #pragma unroll
-      for (int k2 = 0; k2 < SP_R2; ++k2) T[z * SP_ROW + ((4 * k2 + xi) ^ (4 * (z & 7)))] = w[p][k2];
+        for (int k2 = 0; k2 < SP_R2; ++k2) T[colpos<NZ>(2 * k2 + xi, z)] = w[p][k2];
+      }
     }
     __syncthreads();
-    // z transform of column lane = 4 k2 + xi
+    // z transform of column c (this warp's lines only from here on)
     float2 v[N1];
 #pragma unroll
-    for (int q = 0; q < N1; ++q) {
-      const int zz = in_index<NZ>(g, q);
-      v[q] = T[zz * SP_ROW + (lane ^ (4 * (zz & 7)))];
-    }
-    __syncthreads();
-    fft_col32<NZ, false>(v, T, tws, g, lane);
+    for (int q = 0; q < N1; ++q) v[q] = T[colpos<NZ>(c, in_index<NZ>(g, q))];
+    __syncwarp();
+    fft_line<NZ, false>(v, T + c * NZ, tws, g);
     {
-      const int kxx = SP_XB * xb + (lane & 3), ky = k1 + SP_R1 * (lane >> 2);
+      const int kxx = SP_XB * xb + (c & 1), ky = k1 + SP_R1 * (c >> 1);
       const float p2in = axis_p2(sy, 2, kxx) + axis_p2(sy, 1, ky);
       if (sy.table) {
 #pragma unroll
@@ -506,27 +493,28 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
 #pragma unroll
       for (int q = 0; q < N1; ++q) v[q] = tmp[q];
     }
-    fft_col32<NZ, true>(v, T, tws, g, lane);
+    fft_line<NZ, true>(v, T + c * NZ, tws, g);
 #pragma unroll
-    for (int q = 0; q < N1; ++q) {
-      const int zz = out_index<NZ>(g, q);
-      T[zz * SP_ROW + (lane ^ (4 * (zz & 7)))] = v[q];
-    }
+    for (int q = 0; q < N1; ++q) T[colpos<NZ>(c, out_index<NZ>(g, q))] = v[q];
     __syncthreads();
     // inverse y2 stage
 #pragma unroll
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
+      if (z < NZ) {
 #pragma unroll
-      for (int k2 = 0; k2 < SP_R2; ++k2) w[p][k2] = T[z * SP_ROW + ((4 * k2 + xi) ^ (4 * (z & 7)))];
-      DFT<SP_R2, true, float2>::run(w[p]);
+        for (int k2 = 0; k2 < SP_R2; ++k2) w[p][k2] = T[colpos<NZ>(2 * k2 + xi, z)];
+        DFT<SP_R2, true, float2>::run(w[p]);
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
+      if (z < NZ) {
 #pragma unroll
-      for (int y2 = 0; y2 < SP_R2; ++y2) T[z * SP_ROW + (((y2 ^ (z & 3)) << 2) | xi)] = w[p][y2];
+        for (int y2 = 0; y2 < SP_R2; ++y2) T[z * SP_ROW + (((y2 ^ (z & 7)) << 1) | xi)] = w[p][y2];
+      }
     }
     fence_proxy_async_smem();
     __syncthreads();

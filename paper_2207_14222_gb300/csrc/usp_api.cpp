@@ -192,13 +192,13 @@ static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, in
 }
 
 // The scratch in the split-y layout S[k1][xb][z][slot] viewed as 5-D
-// {xi 4, y2 8, z nz, xb 64, k1 32} (8-byte elements); a rows-pass tile (plane
-// z, residue y2) is the box {4, 1, 1, 64, 32}.
+// {xi 2, y2 16, z nz, xb 128, k1 16} (8-byte elements); a rows-pass tile
+// (plane z, residue y2) is the box {2, 1, 1, 128, 16}.
 static bool encode_split_map(CUtensorMap* m, void* base, int nz) {
   if (!tensor_map_encoder()) return false;
-  const cuuint64_t dims[5] = {4, 8, (cuuint64_t)nz, 64, 32};
-  const cuuint64_t strides[4] = {32, 256, (cuuint64_t)nz * 256, (cuuint64_t)nz * 256 * 64};
-  const cuuint32_t box[5] = {4, 1, 1, 64, 32};
+  const cuuint64_t dims[5] = {2, 16, (cuuint64_t)nz, 128, 16};
+  const cuuint64_t strides[4] = {16, 256, (cuuint64_t)nz * 256, (cuuint64_t)nz * 256 * 128};
+  const cuuint32_t box[5] = {2, 1, 1, 128, 16};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 5, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -589,7 +589,7 @@ static SplitArgs split_args(usp_solver* s, const float2* y, const float2* xin, f
 
 static std::function<cudaError_t(cudaStream_t)> split_rows_pass(usp_solver* s, int mode,
                                                                 const SplitArgs& a) {
-  const int grid = (int)std::min<int64_t>((int64_t)s->n[0] * 8, s->num_sms);
+  const int grid = (int)std::min<int64_t>((int64_t)s->n[0] * 16, (int64_t)s->num_sms * 2);
   const CUtensorMap map = s->split_map;
   return [=](cudaStream_t t) { return launch_split_rows(mode, map, a, grid, t); };
 }
