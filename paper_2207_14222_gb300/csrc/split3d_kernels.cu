@@ -113,9 +113,13 @@ __device__ __forceinline__ void load_stage1_twiddles(float2* dst, const float2* 
 // with three 32 KB shared-memory slots:
 //   SU: the tile's scratch values [k1][kx] (one 5-D tensor load); exchange of
 //       the inverse transforms, then refilled with the next tile's values;
-//   SV: V rows [y1][x] (16 bulk copies); refilled after the pointwise step;
+//   SV: V rows [y1][x] (16 bulk copies); refilled once the pointwise step
+//       has read it;
 //   SY: y rows [y1][x] (16 bulk copies); exchange of the forward transforms,
 //       refilled once the forward y1 stage has read it.
+// Each slot is issued exactly once per tile, behind a block barrier that
+// follows its last read; x of the next tile is loaded into registers right
+// after the pointwise step, so its latency overlaps the forward transforms.
 // Thread roles: rows (f = tid / 16 is the row y1, g = tid % 16 its line
 // thread) for the x transform and the pointwise step; columns (kx = tid) for
 // the y1 stage, a 16-point transform in registers.
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     k_split_rows(const __grid_constant__ CUtensorMap smap, const SplitArgs a) {
   constexpr bool POST = MODE != SPLIT_PRE;   // the tile starts from the scratch (inverse part)
   constexpr bool PRE = MODE != SPLIT_POST;   // the tile ends with t = B x + y and its transform
+  constexpr bool FULL = POST && PRE;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* SU = reinterpret_cast<float2*>(smem_raw);
   float2* SV = SU + SA_TILE;
@@ -250,8 +255,16 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
       for (int q = 0; q < 16; ++q) v[q] = SU[f * SP_N + 16 * q + g];
       __syncwarp();   // row f (this warp's) is read before its exchange reuses it
       fft_line<256, true>(v, SU + f * SP_N, tws, g);   // u at x = g + 16 q
-      release_then(0, k + 1);
-      wait_bars(PRE ? 2 : 1, par);
+      if (FULL) {
+        // the next scratch tile goes into SU behind the barrier of the V and
+        // y waits (every warp has finished its inverse transform by then)
+        fence_proxy_async_smem();
+        wait_bars(2, par);
+        if (tid < 32 && k + 1 < my) issue(0, k + 1);
+      } else {
+        release_then(0, k + 1);
+        wait_bars(1, par);
+      }
       if (!ok) break;
       // Delta = (1-V)(u - x); x += alpha Delta; next t = (1-V) x + y
 #pragma unroll
@@ -269,10 +282,10 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
           v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
         }
       }
-      release_then(1, k + 1);
-      // with POST the next x is read at the end of this tile: the inverse
-      // part of the next tile covers its latency
-      if (!PRE && k + 1 < my) prefetch_x(k + 1);
+      // FULL: the next V tile is issued behind the barrier that follows the
+      // forward x transform (SV is read only above)
+      if (!FULL) release_then(1, k + 1);
+      if (k + 1 < my) prefetch_x(k + 1);
     } else {
       wait_bars(2, par);
       if (!ok) break;
@@ -296,7 +309,9 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
       fft_line<256, false>(v, SY + f * SP_N, tws, g);
 #pragma unroll
       for (int q = 0; q < 16; ++q) SY[f * SP_N + g + 16 * q] = v[q];
+      fence_proxy_async_smem();
       __syncthreads();
+      if (FULL && tid < 32 && k + 1 < my) issue(1, k + 1);
       // forward y1 stage: 16-point DFT over the rows, then W_256^(y2 k1)
       float2 c[16];
 #pragma unroll
@@ -307,7 +322,6 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
       const int64_t k1_stride = (int64_t)SP_NXB * a.nz * SP_ROW;
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) dst[k1 * k1_stride] = cmul(c[k1], w256[(y2 * k1) & 255]);
-      if (POST && k + 1 < my) prefetch_x(k + 1);
     }
   }
 
