@@ -242,9 +242,10 @@ def schedule_efficiency(passes, points, vreal, iteration_ms, peak):
             "iter_per_s_at_iteration_ms": 1e3 / iteration_ms}
 
 
-# Sources of the pencil-schedule kernels whose ncu traffic is recorded.
+# Sources of the 3-D pass kernels (pencil and split-y schedules) whose ncu
+# traffic is recorded.
 PENCIL_SOURCES = ("fft_core.cuh", "iteration_state.cuh", "kernels.h", "pencil_kernels.cu",
-                  "tma.cuh", "tma_kernels.cu")
+                  "tma.cuh", "tma_kernels.cu", "split3d_kernels.cu")
 
 
 def kernel_sources_sha():

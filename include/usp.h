@@ -113,7 +113,8 @@ typedef struct {
   int32_t plain;
   /* 0: automatic (on-chip where it applies, except batches of 192^2 and
    *    256^2 problems whose clusters do not all fit on the device at once;
-   *    else pencil);
+   *    split-y for single 3-D problems nz x 256 x 256 unless tc_dft or
+   *    no_tma is set; else pencil);
    * 1: pencil schedule (one FFT axis per pass);
    * 2: fused 3-D schedule (two passes per iteration; 3-D grids nz x 256 x
    *    256, single problem);
@@ -507,7 +508,7 @@ usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int32_t iters,
                            usp_pass_time* out, int32_t capacity, int32_t* n_out);
 
 /* Autotuner: time one iteration of each pass variant the solver's grid
- * admits (pencil or fused schedule; TMA-staged or plain-load passes) over
+ * admits (pencil, fused, split or on-chip schedule; TMA-staged or plain-load passes) over
  * `iters` iterations on (y, x) (device pointers; x is overwritten), keep the
  * fastest, and size the iterations per CUDA-graph launch (chunk) to about
  * 0.2 ms of GPU work.  The choice is cached per (grid, batch count, real or

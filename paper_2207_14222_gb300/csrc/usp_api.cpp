@@ -561,11 +561,15 @@ static std::vector<PassLaunch> fused_passes(usp_solver* s, const float2* y, cons
 // ---- split-y two-pass schedule (grids nz x 256 x 256, split3d_kernels.cu)
 
 static bool split_supported(const usp_solver* s) { return s->split_ok && s->num_sms > 0; }
-// Schedule 4 selects it; the rows pass bulk-copies rows of y and V and the
-// column pass whole tiles of the scratch, so all three must be 16-byte
-// aligned (otherwise the pencil schedule runs).
+// Schedule 4 selects it; the automatic choice (0) takes it wherever it
+// applies (measured per iteration, split against pencil: nz = 32 52 / 78 us,
+// 64 78 / 108, 128 135 / 159, 256 249 / 275).  The rows pass bulk-copies rows of y and V and the column pass
+// whole tiles of the scratch, so all three must be 16-byte aligned
+// (otherwise the pencil schedule runs).
 static bool use_split(const usp_solver* s, const float2* y) {
-  if (!split_supported(s) || s->opt.schedule != 4) return false;
+  if (!split_supported(s)) return false;
+  if (s->opt.schedule != 4 && !(s->opt.schedule == 0 && !s->opt.tc_dft && !s->opt.no_tma))
+    return false;
   return (((uintptr_t)y | (uintptr_t)s->V | (uintptr_t)s->buf) & 15u) == 0;
 }
 
@@ -1576,7 +1580,8 @@ extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_
       return st;
     }
   }
-  // candidates: pass schedule x staged (TMA) or plain loads
+  // candidates: pass schedule x staged (TMA) or plain loads; the split and
+  // on-chip schedules where the grid admits them
   std::vector<usp_options> cands;
   const int nx = s->n[s->ndim - 1];
   const bool staged = s->maps_ok || rows_tma_tile_rows(nx) > 0;
@@ -1589,6 +1594,13 @@ extern "C" usp_status usp_autotune(usp_solver* s, const void* y, void* x, int32_
         o.cols_tile = ct;
         cands.push_back(o);
       }
+  if (split_supported(s)) {
+    usp_options o = s->opt;
+    o.schedule = 4;
+    o.no_tma = 0;
+    o.cols_tile = 0;
+    cands.push_back(o);
+  }
   for (int rows = 8; rows <= 16; rows += 8)
     if (onchip_available(s, rows)) {
       usp_options o = s->opt;

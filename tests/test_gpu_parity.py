@@ -200,23 +200,24 @@ def test_fused_warm_start_and_reference_pass(torch_cuda):
     assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= TOL_X
 
 
-def test_parity_full_size_256_bench_configuration(torch_cuda):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_parity_full_size_256_bench_configuration(torch_cuda, schedule):
     """The benchmark's workload (3-D Helmholtz 256^3) in the benchmark's
-    launch configuration (automatic schedule), every output compared with
-    the oracle after 3 iterations."""
+    launch configuration (automatic schedule: the split-y passes) and on the
+    pencil passes, every output compared with the oracle after 3 iterations."""
     shape = (256, 256, 256)
     prob = inputs.helmholtz_3d(256, seed=0)
-    _check_trajectory(torch_cuda, shape, prob, 3)
+    _check_trajectory(torch_cuda, shape, prob, 3, schedule=schedule)
 
 
-def test_parity_full_size_256_diffusion(torch_cuda):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_parity_full_size_256_diffusion(torch_cuda, schedule):
     """The second full-size workload (3-D steady diffusion 256^3, Sec. 3.2 in
-    its scalar form: real float32 V through the staged rows and strided-axis
-    passes), automatic schedule, every output compared with the oracle after
-    4 iterations."""
+    its scalar form: real float32 V), automatic schedule (split-y) and the
+    pencil passes, every output compared with the oracle after 4 iterations."""
     shape = (256, 256, 256)
     prob = inputs.diffusion_3d(256, seed=0)
-    _check_trajectory(torch_cuda, shape, prob, 4, vreal=True)
+    _check_trajectory(torch_cuda, shape, prob, 4, vreal=True, schedule=schedule)
 
 
 @pytest.mark.parametrize("workload", ["helmholtz", "diffusion"])
