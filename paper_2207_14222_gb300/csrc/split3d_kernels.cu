@@ -398,6 +398,15 @@ __device__ __forceinline__ int colpos(int c, int z) {
   return c * NZ + (z ^ (8 * (c & 1)));
 }
 
+// Position in column c of register q of line thread g (input order with IN,
+// else output order).  For NZ = 256 both orders are g + 16 q, and the XOR
+// touches only g, so the position is a per-thread base plus a constant.
+template <int NZ, bool IN>
+__device__ __forceinline__ int zpos(int cbase, int c, int g, int q) {
+  if (Split<NZ>::N2 >= 16 && Split<NZ>::S == 1) return cbase + 16 * q;
+  return colpos<NZ>(c, IN ? in_index<NZ>(g, q) : out_index<NZ>(g, q));
+}
+
 template <int NZ>
 __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     k_split_cols(const SplitColsArgs a) {
@@ -413,6 +422,14 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
   const int tid = threadIdx.x;
   const int c = tid / G, g = tid % G;      // z-transform roles: column c = 2 k2 + xi
   const int xi = tid & 1, zb = tid >> 1;   // y2-stage roles
+  // per-thread offsets (the same in every tile): slot position of y2 = j
+  // and j + 8 (z & 7 is the same for all of this thread's pairs, since
+  // ZSTEP is a multiple of 8), column-major position of k2 = 0, and the
+  // z-transform base of column c
+  int so[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) so[j] = 2 * (j ^ (zb & 7)) + xi;
+  const int cbase = c * NZ + (g ^ (8 * (c & 1)));
   const int64_t t0 = blockIdx.x, stride = gridDim.x;
   const int64_t my = t0 < SC_TILES ? (SC_TILES - t0 + stride - 1) / stride : 0;
   load_stage1_twiddles<NZ>(tws, a.tw);
@@ -459,8 +476,9 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
       if (z < NZ) {
+        const float2* Tz = T + z * SP_ROW;
 #pragma unroll
-        for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = T[z * SP_ROW + (((y2 ^ (z & 7)) << 1) | xi)];
+        for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = Tz[so[y2 & 7] + 16 * (y2 >> 3)];
         DFT<SP_R2, false, float2>::run(w[p]);
       }
     }
@@ -469,15 +487,16 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
       if (z < NZ) {
+        float2* Te = T + colpos<NZ>(xi, z);
 #pragma unroll
-        for (int k2 = 0; k2 < SP_R2; ++k2) T[colpos<NZ>(2 * k2 + xi, z)] = w[p][k2];
+        for (int k2 = 0; k2 < SP_R2; ++k2) Te[2 * NZ * k2] = w[p][k2];
       }
     }
     __syncthreads();
     // z transform of column c (this warp's lines only from here on)
     float2 v[N1];
 #pragma unroll
-    for (int q = 0; q < N1; ++q) v[q] = T[colpos<NZ>(c, in_index<NZ>(g, q))];
+    for (int q = 0; q < N1; ++q) v[q] = T[zpos<NZ, true>(cbase, c, g, q)];
     __syncwarp();
     fft_line<NZ, false>(v, T + c * NZ, tws, g);
     {
@@ -490,6 +509,22 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
           const float dr = l.x + 1.f;
           const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, l.y * l.y));
           v[q] = cmul(v[q], make_float2(dr * sc, -l.y * sc));
+        }
+      } else if (sy.a_re == 0.f) {
+        // Helmholtz form: a purely imaginary, so Re(Lhat + 1) = Re b + 1
+        const float dr2 = b1 * b1;
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+          const float di = fmaf(sy.a_im, p2in + pz2[q], sy.b_im);
+          const float sc = __fdividef(sy.inv_n, fmaf(di, di, dr2));
+          v[q] = cmul(v[q], make_float2(b1 * sc, -di * sc));
+        }
+      } else if (sy.a_im == 0.f && sy.b_im == 0.f) {
+        // real symbol (diffusion): a real factor
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+          const float sc = __fdividef(sy.inv_n, fmaf(sy.a_re, p2in + pz2[q], b1));
+          v[q] = make_float2(v[q].x * sc, v[q].y * sc);
         }
       } else {
         // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
@@ -509,15 +544,16 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     }
     fft_line<NZ, true>(v, T + c * NZ, tws, g);
 #pragma unroll
-    for (int q = 0; q < N1; ++q) T[colpos<NZ>(c, out_index<NZ>(g, q))] = v[q];
+    for (int q = 0; q < N1; ++q) T[zpos<NZ, false>(cbase, c, g, q)] = v[q];
     __syncthreads();
     // inverse y2 stage
 #pragma unroll
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
       if (z < NZ) {
+        const float2* Te = T + colpos<NZ>(xi, z);
 #pragma unroll
-        for (int k2 = 0; k2 < SP_R2; ++k2) w[p][k2] = T[colpos<NZ>(2 * k2 + xi, z)];
+        for (int k2 = 0; k2 < SP_R2; ++k2) w[p][k2] = Te[2 * NZ * k2];
         DFT<SP_R2, true, float2>::run(w[p]);
       }
     }
@@ -526,8 +562,9 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
       if (z < NZ) {
+        float2* Tz = T + z * SP_ROW;
 #pragma unroll
-        for (int y2 = 0; y2 < SP_R2; ++y2) T[z * SP_ROW + (((y2 ^ (z & 7)) << 1) | xi)] = w[p][y2];
+        for (int y2 = 0; y2 < SP_R2; ++y2) Tz[so[y2 & 7] + 16 * (y2 >> 3)] = w[p][y2];
       }
     }
     fence_proxy_async_smem();

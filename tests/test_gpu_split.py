@@ -1,8 +1,8 @@
 """The split-y two-pass schedule (schedule 4: grids nz x 256 x 256) against
 the FP64 oracle, through the C ABI.
 
-The rows pass does the x transform and the 32-point y1 stage of each tile
-of 32 rows (y = 8 y1 + y2); the column pass the 8-point y2 stage, the z
+The rows pass does the x transform and the 16-point y1 stage of each tile
+of 16 rows (y = 16 y1 + y2); the column pass the 16-point y2 stage, the z
 transform and the multiply.  Every test compares element by element with the
 oracle's Algorithm 1 on the same complex64 (or float32) inputs, at the
 complex64 bar (rel-L2 1e-5 on x, 1e-4 on the residual history).
@@ -170,3 +170,23 @@ def test_split_schedule_refuses_other_grids(torch_cuda):
         cf, V, y = _prep(inputs.white_helmholtz(shape, 56))
         with pytest.raises(_lib.UspError):
             Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).cuda(), schedule=4)
+
+
+def test_split_general_complex_symbol(torch_cuda):
+    """A symbol a |p|^2 + b with both a and b complex (neither the Helmholtz
+    form, a purely imaginary, nor the real diffusion form) through the column
+    pass's general multiply."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (32, 256, 256)
+    cf, V, y = _prep(inputs.white_helmholtz(shape, 57))
+    a, b = complex(0.04, 0.25), complex(0.15, -0.35)
+    dev = torch.device("cuda:0")
+    n_iter = 20
+    with Solver(shape, a, b, torch.from_numpy(V).to(dev), dx=cf["dx"], plain=True,
+                schedule=4) as s:
+        x, res = s.solve(torch.from_numpy(y).to(dev), tol=0.0, maxit=n_iter)
+        xg = x.cpu().numpy().astype(np.complex128)
+    Lh = uo.lhat(shape, cf["dx"], a, b)
+    xo, _ = uo.iterate(V.astype(np.complex128), y.astype(np.complex128), Lh, res["alpha"], n_iter)
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL_X
