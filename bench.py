@@ -668,13 +668,14 @@ def mixed_batch_leg(args, torch, dev):
           for n in sides}
     yg = {n: torch.from_numpy(np.stack([cf["y"] for cf in groups[n]])).to(dev) for n in sides}
 
-    def together():
+    def together(which=None):
+        which = sides if which is None else which
         solvers = [BatchSolver((n, n), [cf["a"] for cf in groups[n]],
-                               [cf["b"] for cf in groups[n]], Vg[n]) for n in sides]
+                               [cf["b"] for cf in groups[n]], Vg[n]) for n in which]
         try:
-            for sv, n in zip(solvers, sides):
+            for sv, n in zip(solvers, which):
                 sv.autotune(yg[n], iters=3)
-            _, res = solve_many(solvers, [yg[n] for n in sides], tol=args.tol,
+            _, res = solve_many(solvers, [yg[n] for n in which], tol=args.tol,
                                 maxit=args.maxit)
         finally:
             for sv in solvers:
@@ -724,6 +725,20 @@ def mixed_batch_leg(args, torch, dev):
                      "converged": sum(int(r["converged"]) for r in res),
                      "iterations_min_max": [min(its), max(its)]}
     out["speedup"] = out["one_by_one"]["s"] / out["concurrent_batches"]["s"]
+    # the critical path: each side's batch alone, and the on-chip sides
+    # (one launch per phase each) against the sides on the passes
+    def timed(which):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        together(which)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+    out["side_alone_s"] = {str(n): round(timed([n]), 5) for n in sides}
+    small = [n for n in sides if per_side[str(n)]["schedule"] == "on-chip"]
+    large = [n for n in sides if n not in small]
+    if small and large:
+        out["onchip_sides_together_s"] = round(timed(small), 5)
+        out["pass_sides_together_s"] = round(timed(large), 5)
     return out
 
 

@@ -180,6 +180,22 @@ __global__ void __launch_bounds__(COLS * Split<N>::G, 32 / COLS)
             v[q] = cmul(v[q], table_factor_f(sy.table[kspace_index(sy, out_index<N>(g, q), col,
                                                                    (a.flags & F_CBLOCK) != 0)],
                                              sy, a.mul));
+        } else if (a.mul == MUL_LINV && sy.a_re == 0.f) {
+          // Helmholtz form: a purely imaginary, so Re(Lhat + 1) = Re b + 1
+          const float dr2 = b1 * b1;
+#pragma unroll
+          for (int q = 0; q < N1; ++q) {
+            const float di = fmaf(sy.a_im, p2in + pz2[q], sy.b_im);
+            const float sc = __fdividef(sy.inv_n, fmaf(di, di, dr2));
+            v[q] = cmul(v[q], make_float2(b1 * sc, -di * sc));
+          }
+        } else if (a.mul == MUL_LINV && sy.a_im == 0.f && sy.b_im == 0.f) {
+          // real symbol (diffusion): a real factor
+#pragma unroll
+          for (int q = 0; q < N1; ++q) {
+            const float sc = __fdividef(sy.inv_n, fmaf(sy.a_re, p2in + pz2[q], b1));
+            v[q] = make_float2(v[q].x * sc, v[q].y * sc);
+          }
         } else if (a.mul == MUL_LINV) {
           // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
 #pragma unroll
