@@ -251,7 +251,7 @@ cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t 
 // nz in {32, 64, 128, 256}: the rows pass does the x transform and the
 // 16-point y1 stage of each tile (plane z, rows y = 16 y1 + y2); the column
 // pass the 16-point y2 stage, the z transform and the spectral multiply.
-// Scratch layout S[k1][xb][z][((y2 ^ (z & 7)) << 1) | xi], kx = 2 xb + xi.
+// Scratch layout S[z][y2][k1][kx].
 enum SplitMode : int {
   SPLIT_PRE = 0,    // t = (1-V) x + y ; forward x and y1 stages      (phase prologue)
   SPLIT_FULL = 1,   // inverse y1, x ; Delta, update, norm ; next t ; forward x, y1
@@ -273,7 +273,7 @@ struct SplitArgs {
 };
 struct SplitColsArgs {
   int flags;            // F_REVERSE
-  float2* buf;          // scratch in the split layout (16-byte aligned)
+  float2* buf;          // scratch in the split layout
   const float2* tw;     // W_256^m table (device)
   DevState* st;
   Sym<float> sym;       // quadratic symbol or table (k-space C order)
@@ -281,10 +281,11 @@ struct SplitColsArgs {
 cudaError_t split_init();
 bool split_nz_ok(int nz);
 int split_cols_ctas_per_sm(int nz);
-// map: the scratch viewed as 5-D {xi 2, y2 16, z nz, xb 128, k1 16}, box {2, 1, 1, 128, 16}.
-cudaError_t launch_split_rows(int mode, const CUtensorMap& map, const SplitArgs& a, int grid,
+cudaError_t launch_split_rows(int mode, const SplitArgs& a, int grid, cudaStream_t s);
+// map: the scratch viewed as 4-D {kx 256, z nz, y2 16, k1 16} (8-byte
+// elements, strides in that order 524288 / 32768 / 2048 bytes), box {2, nz, 16, 1}.
+cudaError_t launch_split_cols(int nz, const CUtensorMap& map, const SplitColsArgs& a, int grid,
                               cudaStream_t s);
-cudaError_t launch_split_cols(int nz, const SplitColsArgs& a, int grid, cudaStream_t s);
 
 // Launchers (pencil_kernels.cu).  n = transform length (power of two, 2..256).
 cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaStream_t s);

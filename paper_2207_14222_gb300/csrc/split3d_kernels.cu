@@ -20,16 +20,19 @@
 // y; write x, scratch; 44 with a real V) + columns 16 = 64, against 96 for the
 // pencil schedule.
 //
-// Scratch layout (complex64), chosen so that a column tile is one contiguous
+// Scratch layout (complex64), chosen so that a rows tile is one contiguous
 // block:
-//   S[k1][xb][z][slot],  kx = 2 xb + xi,  slot = ((y2 ^ (z & 7)) << 1) | xi,
-// 32 values (256 bytes) per (k1, xb, z).  The rows pass reads and writes it in
-// 16-byte pieces (the two kx of a column tile); the XOR puts the y2 groups of
-// neighbouring z rows on different shared-memory banks in the column pass.
+//   S[z][y2][k1][kx]  (a rows tile (z, y2) is 16 x 256 values, 32 KB).
+// The rows pass reads its tile with one bulk copy and writes it with
+// coalesced stores; the column pass gathers its tile (k1, two kx, all y2 and
+// z) with one 4-D tensor load of 16-byte pieces and scatters it back with one
+// tensor store.  The tensor map lists z before y2, so the tile arrives in
+// shared memory as [y2][z][xi]: a warp's 16 z x 2 xi of one y2 are 256
+// consecutive bytes.
 //
-// Both kernels are persistent and stage their tiles with the copy engine
-// (bulk copies and one 5-D tensor load); every wait is bounded and a wait that
-// gives up marks the solve ST_TIMEOUT after the copies in flight have landed.
+// Both kernels are persistent and stage their tiles with the copy engine;
+// every wait is bounded and a wait that gives up marks the solve ST_TIMEOUT
+// after the copies in flight have landed.
 #include "fft_core.cuh"
 #include "iteration_state.cuh"
 #include "kernels.h"
@@ -44,27 +47,29 @@ constexpr int SP_R1 = 16;           // y1 points (rows pass)
 constexpr int SP_R2 = 16;           // y2 points (column pass)
 constexpr int SP_XB = 2;            // kx per column tile
 constexpr int SP_NXB = SP_N / SP_XB;
-constexpr int SP_ROW = SP_R2 * SP_XB;   // values per (k1, xb, z)
+constexpr int SP_ROW = SP_R2 * SP_XB;   // values per z of a column tile
 constexpr int SA_THREADS = 256;         // 16 rows x 16 line threads = 256 kx
 constexpr int SA_TILE = SP_R1 * SP_N;   // values per rows tile
 constexpr uint32_t SA_TILE_BYTES = SA_TILE * sizeof(float2);
 constexpr int SC_TILES = SP_R1 * SP_NXB;   // column tiles (k1, xb)
 
-// 5-D tiled TMA load global -> shared, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            int c3, int c4, uint64_t* bar) {
+// 4-D tiled TMA load global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
 
-// 1-D bulk copy shared -> global (this thread's bulk async-group).
-__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-               "r"(smem_u32(src)), "r"(bytes)
-               : "memory");
+// 4-D tiled TMA store shared -> global (this thread's bulk async-group).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                             const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+      : "memory");
 }
 
 // The N-point transform of one line held by the G = Split<N>::G threads g of
@@ -111,8 +116,8 @@ __device__ __forceinline__ void load_stage1_twiddles(float2* dst, const float2* 
 //
 // Two 256-thread CTAs per SM walk tiles u = (z, y2) (u = 16 z + y2), each
 // with three 32 KB shared-memory slots:
-//   SU: the tile's scratch values [k1][kx] (one 5-D tensor load); exchange of
-//       the inverse transforms, then refilled with the next tile's values;
+//   SU: the tile's scratch values [k1][kx] (one bulk copy); exchange of the
+//       inverse transforms, then refilled with the next tile's values;
 //   SV: V rows [y1][x] (16 bulk copies); refilled once the pointwise step
 //       has read it;
 //   SY: y rows [y1][x] (16 bulk copies); exchange of the forward transforms,
@@ -125,7 +130,7 @@ __device__ __forceinline__ void load_stage1_twiddles(float2* dst, const float2* 
 // the y1 stage, a 16-point transform in registers.
 template <int MODE>
 __global__ void __launch_bounds__(SA_THREADS, 2)
-    k_split_rows(const __grid_constant__ CUtensorMap smap, const SplitArgs a) {
+    k_split_rows(const SplitArgs a) {
   constexpr bool POST = MODE != SPLIT_PRE;   // the tile starts from the scratch (inverse part)
   constexpr bool PRE = MODE != SPLIT_POST;   // the tile ends with t = B x + y and its transform
   constexpr bool FULL = POST && PRE;
@@ -173,9 +178,8 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     if (lane == 0) ++n_issued[which];
     if (which == 0) {
       if (lane == 0) {
-        const int z = int(u >> 4), y2 = int(u & 15);
         mbar_arrive_expect_tx(&bars[0], SA_TILE_BYTES);
-        tma_load_5d(SU, &smap, 0, y2 ^ (z & 7), z, 0, 0, &bars[0]);
+        bulk_load(SU, a.buf + u * SA_TILE, SA_TILE_BYTES, &bars[0]);
       }
       return;
     }
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
   for (int64_t k = 0; k < my && ok; ++k) {
     const uint32_t par = uint32_t(k & 1);
     const int64_t u = tile_of(k);
-    const int z = int(u >> 4), y2 = int(u & 15);
+    const int y2 = int(u & 15);
     const int64_t row = row_of(u, f);
     float2 v[16];
     if (POST) {
@@ -318,10 +322,9 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
       for (int i = 0; i < 16; ++i) c[i] = SY[i * SP_N + kx];
       release_then(2, k + 1);
       DFT<16, false, float2>::run(c);
-      float2* dst = a.buf + ((int64_t)(kx >> 1) * a.nz + z) * SP_ROW + (((y2 ^ (z & 7)) << 1) | (kx & 1));
-      const int64_t k1_stride = (int64_t)SP_NXB * a.nz * SP_ROW;
+      float2* dst = a.buf + u * SA_TILE + kx;
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) dst[k1 * k1_stride] = cmul(c[k1], w256[(y2 * k1) & 255]);
+      for (int k1 = 0; k1 < 16; ++k1) dst[k1 * SP_N] = cmul(c[k1], w256[(y2 * k1) & 255]);
     }
   }
 
@@ -368,9 +371,10 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
 
 // ---------------------------------------------------------- column pass ---
 //
-// Tiles (k1, xb): the contiguous block S[k1][xb][*][*] of nz x 32 values,
-// moved by 1-D bulk copies through a ring of three slots (two loads in
-// flight while one tile is transformed in its slot).  In the slot, thread
+// Tiles (k1, xb): the values S[z][y2][k1][2 xb + xi] of all z and y2, moved
+// by 4-D tensor copies (16-byte pieces) through a ring of three slots (two
+// loads in flight while one tile is transformed in its slot); in a slot the
+// tile is laid out [y2][z][xi].  In the slot, thread
 // roles change twice: (z, xi) pairs for the 16-point y2 stage, then columns
 // c = 2 k2 + xi, each held by the G threads of one warp, for the z
 // transform.  The values move between the two through the slot itself,
@@ -409,7 +413,7 @@ __device__ __forceinline__ int zpos(int cbase, int c, int g, int q) {
 
 template <int NZ>
 __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
-    k_split_cols(const SplitColsArgs a) {
+    k_split_cols(const __grid_constant__ CUtensorMap cmap, const SplitColsArgs a) {
   typedef SplitCols<NZ> C;
   constexpr int N1 = C::N1, TILE = C::TILE, G = C::G;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -422,13 +426,7 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
   const int tid = threadIdx.x;
   const int c = tid / G, g = tid % G;      // z-transform roles: column c = 2 k2 + xi
   const int xi = tid & 1, zb = tid >> 1;   // y2-stage roles
-  // per-thread offsets (the same in every tile): slot position of y2 = j
-  // and j + 8 (z & 7 is the same for all of this thread's pairs, since
-  // ZSTEP is a multiple of 8), column-major position of k2 = 0, and the
-  // z-transform base of column c
-  int so[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) so[j] = 2 * (j ^ (zb & 7)) + xi;
+  // z-transform base of column c (the same in every tile)
   const int cbase = c * NZ + (g ^ (8 * (c & 1)));
   const int64_t t0 = blockIdx.x, stride = gridDim.x;
   const int64_t my = t0 < SC_TILES ? (SC_TILES - t0 + stride - 1) / stride : 0;
@@ -449,8 +447,9 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
   auto tile_of = [&](int64_t kk) { return rev ? SC_TILES - 1 - (t0 + kk * stride) : t0 + kk * stride; };
   auto issue = [&](int64_t kk) {   // thread 0: tile kk into slot kk % SLOTS
     const int sl = int(kk % C::SLOTS);
+    const int64_t tt = tile_of(kk);
     mbar_arrive_expect_tx(&full[sl], C::TILE_BYTES);
-    bulk_load(slots + sl * TILE, a.buf + tile_of(kk) * TILE, C::TILE_BYTES, &full[sl]);
+    tma_load_4d(slots + sl * TILE, &cmap, int(SP_XB * (tt % SP_NXB)), 0, 0, int(tt / SP_NXB), &full[sl]);
   };
   int64_t ik = 0;
   if (tid == 0)
@@ -476,9 +475,9 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
       if (z < NZ) {
-        const float2* Tz = T + z * SP_ROW;
+        const float2* Tz = T + z * SP_XB + xi;
 #pragma unroll
-        for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = Tz[so[y2 & 7] + 16 * (y2 >> 3)];
+        for (int y2 = 0; y2 < SP_R2; ++y2) w[p][y2] = Tz[y2 * NZ * SP_XB];
         DFT<SP_R2, false, float2>::run(w[p]);
       }
     }
@@ -562,15 +561,15 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     for (int p = 0; p < C::PAIRS; ++p) {
       const int z = zb + p * C::ZSTEP;
       if (z < NZ) {
-        float2* Tz = T + z * SP_ROW;
+        float2* Tz = T + z * SP_XB + xi;
 #pragma unroll
-        for (int y2 = 0; y2 < SP_R2; ++y2) Tz[so[y2 & 7] + 16 * (y2 >> 3)] = w[p][y2];
+        for (int y2 = 0; y2 < SP_R2; ++y2) Tz[y2 * NZ * SP_XB] = w[p][y2];
       }
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
-      bulk_store(a.buf + t * TILE, T, C::TILE_BYTES);
+      tma_store_4d(&cmap, SP_XB * xb, 0, 0, k1, T);
       bulk_commit();
       if (ik < my) {
         // the slot of tile k+2 held tile k-1, whose store was committed one
@@ -629,30 +628,31 @@ int split_cols_ctas_per_sm(int nz) {
   }
 }
 
-cudaError_t launch_split_rows(int mode, const CUtensorMap& map, const SplitArgs& a, int grid,
-                              cudaStream_t s) {
+cudaError_t launch_split_rows(int mode, const SplitArgs& a, int grid, cudaStream_t s) {
   const size_t sm = split_rows_smem();
   switch (mode) {
-    case SPLIT_PRE: k_split_rows<SPLIT_PRE><<<grid, SA_THREADS, sm, s>>>(map, a); break;
-    case SPLIT_FULL: k_split_rows<SPLIT_FULL><<<grid, SA_THREADS, sm, s>>>(map, a); break;
-    case SPLIT_POST: k_split_rows<SPLIT_POST><<<grid, SA_THREADS, sm, s>>>(map, a); break;
+    case SPLIT_PRE: k_split_rows<SPLIT_PRE><<<grid, SA_THREADS, sm, s>>>(a); break;
+    case SPLIT_FULL: k_split_rows<SPLIT_FULL><<<grid, SA_THREADS, sm, s>>>(a); break;
+    case SPLIT_POST: k_split_rows<SPLIT_POST><<<grid, SA_THREADS, sm, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <int NZ>
-static cudaError_t split_cols_go(const SplitColsArgs& a, int grid, cudaStream_t s) {
-  k_split_cols<NZ><<<grid, SplitCols<NZ>::THREADS, split_cols_smem<NZ>(), s>>>(a);
+static cudaError_t split_cols_go(const CUtensorMap& map, const SplitColsArgs& a, int grid,
+                                 cudaStream_t s) {
+  k_split_cols<NZ><<<grid, SplitCols<NZ>::THREADS, split_cols_smem<NZ>(), s>>>(map, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_cols(int nz, const SplitColsArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_split_cols(int nz, const CUtensorMap& map, const SplitColsArgs& a, int grid,
+                              cudaStream_t s) {
   switch (nz) {
-    case 32: return split_cols_go<32>(a, grid, s);
-    case 64: return split_cols_go<64>(a, grid, s);
-    case 128: return split_cols_go<128>(a, grid, s);
-    case 256: return split_cols_go<256>(a, grid, s);
+    case 32: return split_cols_go<32>(map, a, grid, s);
+    case 64: return split_cols_go<64>(map, a, grid, s);
+    case 128: return split_cols_go<128>(map, a, grid, s);
+    case 256: return split_cols_go<256>(map, a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -142,7 +142,7 @@ struct usp_solver {
   bool maps_ok = false;            // TMA tensor maps of the scratch field
   CUtensorMap map_ax[3][2];        // [tile 32 / 16 / 8 columns][axis]: strided-axis views of s->buf
   bool split_ok = false;           // split_map encoded (grids nz x 256 x 256)
-  CUtensorMap split_map;           // the scratch in the split layout, 5-D (rows-pass tiles)
+  CUtensorMap split_map;           // the scratch in the split layout, 4-D (column-pass tiles)
 };
 
 // Column-tile width of the staged strided-axis passes when the options leave
@@ -191,16 +191,17 @@ static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, in
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The scratch in the split-y layout S[k1][xb][z][slot] viewed as 5-D
-// {xi 2, y2 16, z nz, xb 128, k1 16} (8-byte elements); a rows-pass tile
-// (plane z, residue y2) is the box {2, 1, 1, 128, 16}.
+// The scratch in the split-y layout S[z][y2][k1][kx] viewed as 4-D
+// {kx 256, z nz, y2 16, k1 16} (8-byte elements; z listed before y2 so that
+// a column tile lands in shared memory as [y2][z][xi]); a column-pass tile
+// (k1, two kx) is the box {2, nz, 16, 1}.
 static bool encode_split_map(CUtensorMap* m, void* base, int nz) {
   if (!tensor_map_encoder()) return false;
-  const cuuint64_t dims[5] = {2, 16, (cuuint64_t)nz, 128, 16};
-  const cuuint64_t strides[4] = {16, 256, (cuuint64_t)nz * 256, (cuuint64_t)nz * 256 * 128};
-  const cuuint32_t box[5] = {2, 1, 1, 128, 16};
-  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 5, base, dims, strides, box, estr,
+  const cuuint64_t dims[4] = {256, (cuuint64_t)nz, 16, 16};
+  const cuuint64_t strides[3] = {16 * 16 * 256 * 8, 16 * 256 * 8, 256 * 8};
+  const cuuint32_t box[4] = {2, (cuuint32_t)nz, 16, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -562,8 +563,8 @@ static std::vector<PassLaunch> fused_passes(usp_solver* s, const float2* y, cons
 
 static bool split_supported(const usp_solver* s) { return s->split_ok && s->num_sms > 0; }
 // Schedule 4 selects it; the automatic choice (0) takes it wherever it
-// applies (measured per iteration, split against pencil: nz = 32 52 / 78 us,
-// 64 78 / 108, 128 135 / 159, 256 249 / 275).  The rows pass bulk-copies rows of y and V and the column pass
+// applies (measured per iteration, split against pencil: nz = 32 48 / 78 us,
+// 64 72 / 110, 128 126 / 164, 256 222 / 279).  The rows pass bulk-copies rows of y and V and the column pass
 // whole tiles of the scratch, so all three must be 16-byte aligned
 // (otherwise the pencil schedule runs).
 static bool use_split(const usp_solver* s, const float2* y) {
@@ -594,8 +595,7 @@ static SplitArgs split_args(usp_solver* s, const float2* y, const float2* xin, f
 static std::function<cudaError_t(cudaStream_t)> split_rows_pass(usp_solver* s, int mode,
                                                                 const SplitArgs& a) {
   const int grid = (int)std::min<int64_t>((int64_t)s->n[0] * 16, (int64_t)s->num_sms * 2);
-  const CUtensorMap map = s->split_map;
-  return [=](cudaStream_t t) { return launch_split_rows(mode, map, a, grid, t); };
+  return [=](cudaStream_t t) { return launch_split_rows(mode, a, grid, t); };
 }
 
 static std::vector<PassLaunch> split_prologue(usp_solver* s, const float2* y, const float2* xin,
@@ -619,7 +619,9 @@ static std::vector<PassLaunch> split_passes(usp_solver* s, const float2* y, cons
   c.sym = s->symf;
   const int nz = s->n[0];
   const int cgrid = s->num_sms * split_cols_ctas_per_sm(nz);
-  P.push_back({"split_cols", 16.0, [=](cudaStream_t t) { return launch_split_cols(nz, c, cgrid, t); }});
+  const CUtensorMap cmap = s->split_map;
+  P.push_back({"split_cols", 16.0,
+               [=](cudaStream_t t) { return launch_split_cols(nz, cmap, c, cgrid, t); }});
   SplitArgs a = split_args(s, y, xin, xout, flags);
   if (ref) P.push_back({"split_rows_post", 8.0 + vb, split_rows_pass(s, SPLIT_POST, a)});
   else P.push_back({"split_rows_full", 32.0 + vb + (xz ? 0.0 : 8.0), split_rows_pass(s, SPLIT_FULL, a)});
