@@ -251,7 +251,7 @@ cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t 
 // nz in {32, 64, 128, 256}: the rows pass does the x transform and the
 // 16-point y1 stage of each tile (plane z, rows y = 16 y1 + y2); the column
 // pass the 16-point y2 stage, the z transform and the spectral multiply.
-// Scratch layout S[z][y2][k1][kx].
+// Scratch layout S[k1][z][y2][kx].
 enum SplitMode : int {
   SPLIT_PRE = 0,    // t = (1-V) x + y ; forward x and y1 stages      (phase prologue)
   SPLIT_FULL = 1,   // inverse y1, x ; Delta, update, norm ; next t ; forward x, y1
@@ -283,7 +283,7 @@ bool split_nz_ok(int nz);
 int split_cols_ctas_per_sm(int nz);
 cudaError_t launch_split_rows(int mode, const SplitArgs& a, int grid, cudaStream_t s);
 // map: the scratch viewed as 4-D {kx 256, z nz, y2 16, k1 16} (8-byte
-// elements, strides in that order 524288 / 32768 / 2048 bytes), box {2, nz, 16, 1}.
+// elements, strides in that order 32768 / 2048 / nz * 32768 bytes), box {2, nz, 16, 1}.
 cudaError_t launch_split_cols(int nz, const CUtensorMap& map, const SplitColsArgs& a, int grid,
                               cudaStream_t s);
 

@@ -20,15 +20,19 @@
 // y; write x, scratch; 44 with a real V) + columns 16 = 64, against 96 for the
 // pencil schedule.
 //
-// Scratch layout (complex64), chosen so that a rows tile is one contiguous
-// block:
-//   S[z][y2][k1][kx]  (a rows tile (z, y2) is 16 x 256 values, 32 KB).
-// The rows pass reads its tile with one bulk copy and writes it with
-// coalesced stores; the column pass gathers its tile (k1, two kx, all y2 and
-// z) with one 4-D tensor load of 16-byte pieces and scatters it back with one
-// tensor store.  The tensor map lists z before y2, so the tile arrives in
-// shared memory as [y2][z][xi]: a warp's 16 z x 2 xi of one y2 are 256
-// consecutive bytes.
+// Scratch layout (complex64), chosen so that a column tile lies inside one
+// k1 slab:
+//   S[k1][z][y2][kx]  (a k1 slab is nz x 16 rows of 256 values, 8 MB at
+//                      nz = 256).
+// The rows pass reads its tile (z, y2) as 16 bulk copies of 2 KB rows, one
+// per k1, and writes it back with coalesced 2 KB stores; the column pass
+// gathers its tile (k1, two kx, all y2 and z) with one 4-D tensor load of
+// 16-byte pieces and scatters it back with one tensor store.  The pieces of
+// one column tile then span one 8 MB slab (a few address-translation pages)
+// instead of the whole 128 MB field, and the tiles in flight at one time
+// (consecutive xb of one or two k1) share their slabs.  The tensor map lists
+// z before y2, so the tile arrives in shared memory as [y2][z][xi]: a warp's
+// 16 z x 2 xi of one y2 are 256 consecutive bytes.
 //
 // Both kernels are persistent and stage their tiles with the copy engine;
 // every wait is bounded and a wait that gives up marks the solve ST_TIMEOUT
@@ -116,7 +120,7 @@ __device__ __forceinline__ void load_stage1_twiddles(float2* dst, const float2* 
 //
 // Two 256-thread CTAs per SM walk tiles u = (z, y2) (u = 16 z + y2), each
 // with three 32 KB shared-memory slots:
-//   SU: the tile's scratch values [k1][kx] (one bulk copy); exchange of the
+//   SU: the tile's scratch values [k1][kx] (16 bulk copies); exchange of the
 //       inverse transforms, then refilled with the next tile's values;
 //   SV: V rows [y1][x] (16 bulk copies); refilled once the pointwise step
 //       has read it;
@@ -177,10 +181,11 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     const int64_t u = tile_of(k);
     if (lane == 0) ++n_issued[which];
     if (which == 0) {
-      if (lane == 0) {
-        mbar_arrive_expect_tx(&bars[0], SA_TILE_BYTES);
-        bulk_load(SU, a.buf + u * SA_TILE, SA_TILE_BYTES, &bars[0]);
-      }
+      // the tile's 16 k1 rows, one k1 slab apart
+      if (lane == 0) mbar_arrive_expect_tx(&bars[0], SA_TILE_BYTES);
+      __syncwarp();
+      if (lane < SP_R1)
+        bulk_load(SU + lane * SP_N, a.buf + (lane * tiles + u) * SP_N, SP_N * 8u, &bars[0]);
       return;
     }
     const bool real = which == 1 && vreal;
@@ -322,9 +327,9 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
       for (int i = 0; i < 16; ++i) c[i] = SY[i * SP_N + kx];
       release_then(2, k + 1);
       DFT<16, false, float2>::run(c);
-      float2* dst = a.buf + u * SA_TILE + kx;
+      float2* dst = a.buf + u * SP_N + kx;
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) dst[k1 * SP_N] = cmul(c[k1], w256[(y2 * k1) & 255]);
+      for (int k1 = 0; k1 < 16; ++k1) dst[k1 * tiles * SP_N] = cmul(c[k1], w256[(y2 * k1) & 255]);
     }
   }
 
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
 
 // ---------------------------------------------------------- column pass ---
 //
-// Tiles (k1, xb): the values S[z][y2][k1][2 xb + xi] of all z and y2, moved
+// Tiles (k1, xb): the values S[k1][z][y2][2 xb + xi] of all z and y2, moved
 // by 4-D tensor copies (16-byte pieces) through a ring of three slots (two
 // loads in flight while one tile is transformed in its slot); in a slot the
 // tile is laid out [y2][z][xi].  In the slot, thread

@@ -191,14 +191,15 @@ static bool encode_cols_map(CUtensorMap* m, void* base, int64_t inner, int n, in
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The scratch in the split-y layout S[z][y2][k1][kx] viewed as 4-D
+// The scratch in the split-y layout S[k1][z][y2][kx] viewed as 4-D
 // {kx 256, z nz, y2 16, k1 16} (8-byte elements; z listed before y2 so that
 // a column tile lands in shared memory as [y2][z][xi]); a column-pass tile
 // (k1, two kx) is the box {2, nz, 16, 1}.
 static bool encode_split_map(CUtensorMap* m, void* base, int nz) {
   if (!tensor_map_encoder()) return false;
   const cuuint64_t dims[4] = {256, (cuuint64_t)nz, 16, 16};
-  const cuuint64_t strides[3] = {16 * 16 * 256 * 8, 16 * 256 * 8, 256 * 8};
+  // S[k1][z][y2][kx]: z, y2 and k1 strides in bytes
+  const cuuint64_t strides[3] = {16 * 256 * 8, 256 * 8, (cuuint64_t)nz * 16 * 256 * 8};
   const cuuint32_t box[4] = {2, (cuuint32_t)nz, 16, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, estr,
