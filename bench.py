@@ -7,7 +7,7 @@ absorbing layer 32 px per face, Gaussian beam source), pixel = lambda/4,
 complex64, solved to a relative preconditioned residual of 1e-6.
 
 One step = create the solver (validation, alpha, scratch) + solve to 1e-6
-(reference norm, iterations, FP64 refinement) + destroy, inputs resident in
+(reference norm, iterations, refinement) + destroy, inputs resident in
 HBM.  `value` = iterations per second over the timed steps (all ranks);
 `ms_per_step` = seconds to residual 1e-6 per solve.
 
@@ -244,7 +244,7 @@ def schedule_efficiency(passes, points, vreal, iteration_ms, peak):
 
 # Sources of the 3-D pass kernels (pencil and split-y schedules) whose ncu
 # traffic is recorded.
-PENCIL_SOURCES = ("fft_core.cuh", "iteration_state.cuh", "kernels.h", "pencil_kernels.cu",
+PENCIL_SOURCES = ("fft_core.cuh", "iteration_state.cuh", "kernels.h", "pencil_core.cuh", "pencil_kernels.cu",
                   "tma.cuh", "tma_kernels.cu", "split3d_kernels.cu")
 
 
@@ -353,7 +353,7 @@ def run_ours(args):
                 "workload": workload_name(args),
                 "grid": list(shape),
                 "tol": args.tol,
-                "mode": "plain" if args.plain else "fp32+fp64-refinement",
+                "mode": "plain" if args.plain else "fp32+refinement (residual in double-float)",
                 "schedule": ["auto", "pencil", "fused", "on-chip", "split"][args.schedule],
                 "tma": not args.no_tma,
                 "cols_tile": args.cols_tile or "default",

@@ -16,7 +16,8 @@
  * until ||Delta|| / ||B (L+I)^-1 y|| < tol, with (L+I)^-1 applied as an FFT,
  * a pointwise multiply by 1/(Lhat+1) and an inverse FFT (Eq.
  * laplacian_inverse).  All arithmetic of the iteration is FP32 on the GPU;
- * norms are summed in FP64.
+ * norms are summed in FP64; the refinement residual y - A x is formed in
+ * double-float (pairs of FP32 values, 48-bit significand) or FP64.
  *
  * Conventions for every entry point:
  *   - Fields are C-contiguous, last axis fastest ([n0][n1][n2]); complex
@@ -95,7 +96,7 @@ typedef struct {
 typedef struct {
   int32_t iterations;        /* Delta evaluations, all phases together     */
   int32_t converged;         /* 1 if the last ||Delta||/ref_norm < tol      */
-  int32_t refinements;       /* FP64 residual restarts performed            */
+  int32_t refinements;       /* residual restarts performed (refinement)    */
   int32_t stagnated;         /* 1 if the FP32 iteration stopped improving  */
   double final_rel_residual; /* last ||Delta|| / ref_norm                   */
   double ref_norm;           /* ||B (L+I)^-1 y||, the alpha-free
@@ -106,7 +107,8 @@ typedef struct {
 /* Solver options (usp_solver_set_options).  Zero-initialised = defaults. */
 typedef struct {
   /* 0: refinement on (default) -- when the FP32 iteration reaches 8*tol or
-   *    stops improving, y - A x is formed in FP64 and the same FP32
+   *    stops improving, y - A x is formed in double-float (or FP64, see
+   *    residual_fp64) and the same FP32
    *    iteration continues on the correction z with source y - A x, which
    *    has exactly the same Delta (A + B = L + I, Sec. 2.1); x = x + z.
    * 1: plain -- Algorithm 1 exactly: stop at tol or maxit.                 */
@@ -131,7 +133,7 @@ typedef struct {
   int32_t schedule;
   /* iterations per CUDA-graph launch between convergence polls; 0: auto   */
   int32_t chunk;
-  /* maximum FP64 refinements per solve; 0: default (4)                     */
+  /* maximum refinements per solve; 0: default (4)                          */
   int32_t max_refinements;
   /* 1: strided-axis passes load and store with plain global accesses
    *    instead of TMA-staged tiles (for comparison); 0: TMA (default)      */
@@ -151,6 +153,13 @@ typedef struct {
    * limit, so the solve ends with the bounded-wait error (USP_ERR_CUDA,
    * "timed out") and the solver stays usable                               */
   int32_t test_wait_fault;
+  /* arithmetic of the refinement residual y - A x (and of usp_apply_A and
+   * usp_residual): 0 (default) double-float -- each real number the
+   * unevaluated sum of two FP32 values, a 48-bit significand, built from
+   * exact two-sum / two-product steps; several times faster than FP64 on a
+   * GPU whose FP64 rate is a small fraction of its FP32 rate; 1: FP64.
+   * Both carry the residual far below the FP32 iteration's own floor.     */
+  int32_t residual_fp64;
 } usp_options;
 
 typedef struct usp_solver usp_solver;
@@ -178,7 +187,7 @@ usp_status usp_solver_create(const usp_grid* grid, const usp_lsymbol* lsym,
  *
  * `count` independent problems A_j = L_j + V_j on the same grid, solved
  * together: every pass of Algorithm 1 (Sec. 2.1) runs once over all problems,
- * each with its own symbol, step, convergence test, residual history and FP64
+ * each with its own symbol, step, convergence test, residual history and
  * refinement.  The paper solves one problem at a time; the batch is this
  * library's throughput form of the same iteration, and each problem follows
  * exactly the path it would take alone.
@@ -266,14 +275,16 @@ usp_status usp_solve_host(usp_solver* s, const void* y_host, void* x_host,
 usp_status usp_residual_history(const usp_solver* s, double* host_out,
                                 int32_t capacity, int32_t* n_out);
 
-/* Forward operator A x = L x + V x (Sec. 2, the problem statement), in FP64
- * arithmetic on the GPU, for the unpreconditioned residual ||A x - y||/||y||
+/* Forward operator A x = L x + V x (Sec. 2, the problem statement), in the
+ * refinement residual's arithmetic on the GPU (double-float, or FP64 with
+ * the residual_fp64 option), for the unpreconditioned residual ||A x - y||/||y||
  * of the paper's tables (Sec. 4.1).  x, Ax: device pointers, N complex64;
  * Ax may not alias x. */
 usp_status usp_apply_A(usp_solver* s, const void* x, void* Ax);
 
-/* r = y - A x in FP64 arithmetic (the refinement residual); r is written as
- * complex64 (device pointer) and, if rel_out is not NULL, ||r||/||y|| (FP64)
+/* r = y - A x, the refinement residual (double-float arithmetic, or FP64
+ * with the residual_fp64 option); r is written as complex64 (device
+ * pointer) and, if rel_out is not NULL, ||r||/||y|| (summed in FP64)
  * to *rel_out (host pointer).  r may be NULL when only the norm is wanted. */
 usp_status usp_residual(usp_solver* s, const void* x, const void* y, void* r,
                         double* rel_out);
@@ -317,7 +328,7 @@ usp_status usp_canon_diffusion(const double* eta, double D, const double* S,
  * device memory was handed to another allocator at start-up, or a hot loop
  * that must not call cudaMalloc/cudaFree because they synchronise the
  * device.  Runs the plain fixed-point iteration of this library (FP32, no
- * FP64 refinement), starting from x = 0, on the caller's V, y and x, with
+ * refinement), starting from x = 0, on the caller's V, y and x, with
  * all scratch (one field, partial sums, state, residual history) in a fixed
  * area of USP_NOALLOC_BYTES compiled into the library.  Grids: each axis a
  * power of two in [2, 256], at most USP_NOALLOC_MAX_POINTS points in all;
@@ -355,7 +366,7 @@ usp_status usp_solve_noalloc(const usp_grid* grid, const usp_lsymbol* lsym, cons
  * components per grid point, V a K x K matrix per point and L a K x K
  * matrix of Fourier multipliers.  Fields are K consecutive planes of N =
  * prod(n) complex64 values (component k at offset k N).  FP32 arithmetic,
- * norms in FP64; plain Algorithm 1 (no FP64 refinement).
+ * norms in FP64; plain Algorithm 1 (no refinement).
  *
  * USP_VARIANT_ANTISYMMETRIC (Sec. 2.2, Eq. antisymmetrised), K = 2: for a
  *   raw problem A0 x0 = y0 that is not accretive, A = [[0, -A0^*], [A0, 0]]/c

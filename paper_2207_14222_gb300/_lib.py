@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("max_refinements", c_int32), ("no_tma", c_int32), ("cols_tile", c_int32),
                 ("tc_dft", c_int32),
                 ("onchip_rows", c_int32),
-                ("test_wait_fault", c_int32)]
+                ("test_wait_fault", c_int32),
+                ("residual_fp64", c_int32)]
 
 
 class FnoConfig(ctypes.Structure):

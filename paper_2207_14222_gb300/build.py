@@ -34,6 +34,12 @@ SOURCES = [
     "tc_kernels.cu",
     "onchip_kernels.cu",
     "split3d_kernels.cu",
+    "df_kernels.cu",
+    "df_part_small.cu",
+    "df_part_p128.cu",
+    "df_part_p256.cu",
+    "df_part_p384.cu",
+    "df_part_p512.cu",
 ]
 
 

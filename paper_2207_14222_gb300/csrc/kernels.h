@@ -79,6 +79,25 @@ enum MulKind : int {
 };
 
 // Spectral symbol Lhat(p) = a |p|^2 + b on the grid; p_ax = ks[ax] * m_ax.
+// Double-float: a real number as the unevaluated sum hi + lo of two floats,
+// |lo| <= ulp(hi)/2 (a 48-bit significand); the arithmetic is in
+// dfloat.cuh.  The working type of the refinement residual's transforms.
+struct __align__(8) dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dfl(float v) : hi(v), lo(0.f) {}
+  // exact for |v| < 2^24 (frequency indices)
+  __host__ __device__ constexpr dfl(int v) : hi((float)v), lo(0.f) {}
+  // the double split into its nearest float and the float nearest the rest
+  __host__ __device__ constexpr dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) dfl2 {
+  dfl x, y;
+};
+
 template <typename T>
 struct Sym {
   T a_re, a_im, b_re, b_im;
@@ -292,12 +311,17 @@ cudaError_t launch_rows_f32(int n, const RowsArgs<float>& a, int64_t grid, cudaS
 cudaError_t launch_rows_f64(int n, const RowsArgs<double>& a, int64_t grid, cudaStream_t s);
 cudaError_t launch_cols_f32(int n, const ColsArgs<float>& a, cudaStream_t s);
 cudaError_t launch_cols_f64(int n, const ColsArgs<double>& a, cudaStream_t s);
+// The same passes in double-float (df_kernels.cu): the refinement residual.
+cudaError_t launch_rows_df(int n, const RowsArgs<dfl>& a, int64_t grid, cudaStream_t s);
+cudaError_t launch_cols_df(int n, const ColsArgs<dfl>& a, cudaStream_t s);
 int rows_per_block_f32(int n);
 int rows_per_block_f64(int n);
 int cols_per_block(int n);   // columns per block of the plain strided-axis pass
 
 // Auxiliary kernels (pencil_kernels.cu).
 cudaError_t init_twiddles();
+// The double-float twiddle tables from the FP64 ones (W_256^m, W_1536^m).
+cudaError_t init_twiddles_df(const double2* tw256, const double2* tw1536);
 // Per-block statistics of V (max |V|, min Re 1/(1-V), nonfinite count) then
 // their reduction into out[3] (device).
 cudaError_t launch_v_stats(const void* V, int vreal, int64_t n, double* partials,

@@ -664,14 +664,37 @@ static cudaError_t enqueue_iteration(usp_solver* s, const float2* y, const float
   return cudaSuccess;
 }
 
-// r = y - A x (or A x with apply_a) in FP64; norms into s->red[0..1].
-static usp_status enqueue_residual64(usp_solver* s, const float2* x, const float2* y, float2* rout,
-                                     bool apply_a) {
+static_assert(sizeof(dfl2) == sizeof(double2), "the residual scratch holds 16-byte values");
+
+// The FP64 symbol in double-float words.
+static Sym<dfl> sym_df(const Sym<double>& d) {
+  Sym<dfl> s{};
+  s.a_re = dfl(d.a_re);
+  s.a_im = dfl(d.a_im);
+  s.b_re = dfl(d.b_re);
+  s.b_im = dfl(d.b_im);
+  s.inv_n = dfl(d.inv_n);
+  for (int i = 0; i < 3; ++i) {
+    s.ks[i] = dfl(d.ks[i]);
+    s.n[i] = d.n[i];
+  }
+  s.ndim = d.ndim;
+  s.table = d.table;
+  return s;
+}
+
+// r = y - A x (or A x with apply_a) in T (FP64 or double-float, 16 bytes per
+// complex value in s->buf64); norms into s->red[0..1].
+template <typename T>
+static usp_status enqueue_residual_t(usp_solver* s, const float2* x, const float2* y, float2* rout,
+                                     bool apply_a, const Sym<T>& sym,
+                                     cudaError_t (*rows)(int, const RowsArgs<T>&, int64_t, cudaStream_t),
+                                     cudaError_t (*cols)(int, const ColsArgs<T>&, cudaStream_t)) {
   if (!s->buf64) CUDA_TRY(cudaMalloc(&s->buf64, sizeof(double2) * s->NB));
   const int vflag = s->vreal ? F_VREAL : 0;
   const int nd = s->ndim;
   const int nx = s->n[nd - 1];
-  RowsArgs<double> r{};
+  RowsArgs<T> r{};
   r.flags = F_NOSTATE | vflag | (apply_a ? F_APPLY_A : 0);
   r.nrows = s->NB / nx;
   r.bt = batch_desc(s, 1);
@@ -682,33 +705,42 @@ static usp_status enqueue_residual64(usp_solver* s, const float2* x, const float
   r.r_out = rout;
   r.partials = s->partials;
   r.st = s->st;
-  r.sym = s->symd;
+  r.sym = sym;
   r.mul = MUL_L;
-  const int64_t grid = rows_grid_f64(s);
+  const int64_t grid = rows_grid_f64(s);   // the same row blocks for both types
   if (nd == 1) {
     r.mode = R_IN_X | R_FWD | R_MUL | R_INV | R_OUT_RESID;
-    CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
+    CUDA_TRY(rows(nx, r, grid, s->stream));
   } else {
     r.mode = R_IN_X | R_FWD | R_OUT_BUF;
-    CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
+    CUDA_TRY(rows(nx, r, grid, s->stream));
     if (nd == 2) {
-      auto c = cols_args<double>(s, 0, COL_FWD_MUL_INV, MUL_L, F_NOSTATE, s->buf64, s->symd);
-      CUDA_TRY(launch_cols_f64(s->n[0], c, s->stream));
+      auto c = cols_args<T>(s, 0, COL_FWD_MUL_INV, MUL_L, F_NOSTATE, s->buf64, sym);
+      CUDA_TRY(cols(s->n[0], c, s->stream));
     } else {
-      auto c1 = cols_args<double>(s, 1, COL_FWD, MUL_L, F_NOSTATE, s->buf64, s->symd);
-      CUDA_TRY(launch_cols_f64(s->n[1], c1, s->stream));
-      auto c0 = cols_args<double>(s, 0, COL_FWD_MUL_INV, MUL_L, F_NOSTATE, s->buf64, s->symd);
-      CUDA_TRY(launch_cols_f64(s->n[0], c0, s->stream));
-      auto c2 = cols_args<double>(s, 1, COL_INV, MUL_L, F_NOSTATE, s->buf64, s->symd);
-      CUDA_TRY(launch_cols_f64(s->n[1], c2, s->stream));
+      auto c1 = cols_args<T>(s, 1, COL_FWD, MUL_L, F_NOSTATE, s->buf64, sym);
+      CUDA_TRY(cols(s->n[1], c1, s->stream));
+      auto c0 = cols_args<T>(s, 0, COL_FWD_MUL_INV, MUL_L, F_NOSTATE, s->buf64, sym);
+      CUDA_TRY(cols(s->n[0], c0, s->stream));
+      auto c2 = cols_args<T>(s, 1, COL_INV, MUL_L, F_NOSTATE, s->buf64, sym);
+      CUDA_TRY(cols(s->n[1], c2, s->stream));
     }
     r.mode = R_IN_BUF | R_INV | R_OUT_RESID;
-    CUDA_TRY(launch_rows_f64(nx, r, grid, s->stream));
+    CUDA_TRY(rows(nx, r, grid, s->stream));
   }
   // per-problem sums of the block partials (blocks never straddle problems)
   CUDA_TRY(launch_sum_pairs(s->partials, (int)(grid / s->B), s->B, s->red, s->stream));
   g_launches.fetch_add(nd == 1 ? 2 : (nd == 2 ? 4 : 6));
   return USP_OK;
+}
+
+// r = y - A x (or A x with apply_a): double-float unless the options ask
+// for FP64.
+static usp_status enqueue_residual64(usp_solver* s, const float2* x, const float2* y, float2* rout,
+                                     bool apply_a) {
+  if (s->opt.residual_fp64)
+    return enqueue_residual_t<double>(s, x, y, rout, apply_a, s->symd, launch_rows_f64, launch_cols_f64);
+  return enqueue_residual_t<dfl>(s, x, y, rout, apply_a, sym_df(s->symd), launch_rows_df, launch_cols_df);
 }
 
 // --------------------------------------------------------- create etc. ---

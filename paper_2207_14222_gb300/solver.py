@@ -43,11 +43,13 @@ class Solver:
     lhat_table : complex64 CUDA tensor of Lhat on the grid's frequencies (FFT
             order) instead of a |p|^2 + b.
     onchip_rows : rows per CTA of the on-chip schedule (8, 16; 0 default).
+    residual_fp64 : True forms the refinement residual (and apply_A, residual)
+            in FP64 instead of double-float.
     """
 
     def __init__(self, shape, a, b, V, alpha=0.0, dx=1.0, stream=None, plain=False,
                  schedule=0, chunk=0, max_refinements=0, no_tma=False, cols_tile=0,
-                 tc_dft=False, lhat_table=None, onchip_rows=0):
+                 tc_dft=False, lhat_table=None, onchip_rows=0, residual_fp64=False):
         """Lhat(p) = a |p|^2 + b, or, with `lhat_table` (a complex64 CUDA tensor of the
         grid's shape, k-space in FFT order), the tabulated symbol; a and b are then
         ignored."""
@@ -87,13 +89,14 @@ class Solver:
         self._h = h
         self.set_options(plain=plain, schedule=schedule, chunk=chunk,
                          max_refinements=max_refinements, no_tma=no_tma, cols_tile=cols_tile,
-                         tc_dft=tc_dft, onchip_rows=onchip_rows)
+                         tc_dft=tc_dft, onchip_rows=onchip_rows, residual_fp64=residual_fp64)
 
     def set_options(self, plain=False, schedule=0, chunk=0, max_refinements=0, no_tma=False,
-                    cols_tile=0, tc_dft=False, onchip_rows=0, test_wait_fault=False):
+                    cols_tile=0, tc_dft=False, onchip_rows=0, test_wait_fault=False,
+                    residual_fp64=False):
         o = Options(int(bool(plain)), int(schedule), int(chunk), int(max_refinements),
                     int(bool(no_tma)), int(cols_tile), int(bool(tc_dft)), int(onchip_rows),
-                    int(bool(test_wait_fault)))
+                    int(bool(test_wait_fault)), int(bool(residual_fp64)))
         check(_lib.lib().usp_solver_set_options(self._h, ctypes.byref(o)))
 
     @property

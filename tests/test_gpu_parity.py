@@ -412,6 +412,43 @@ def test_apply_A_and_residual_fp64(torch_cuda):
         assert rel == pytest.approx(np.linalg.norm(ro) / np.linalg.norm(y), rel=1e-9)
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+def test_refinement_residual_below_fp32_rounding(torch_cuda, fp64):
+    """The refinement residual r = y - A x with y = A x up to complex64
+    rounding, so that ||r|| is about 1e-7 ||y||: r comes out right only if
+    the residual's arithmetic carries far more than FP32 (the same residual
+    with complex64 transforms is checked to miss it).  Double-float (default)
+    and FP64; line lengths 384 (radix-3 lines), 96 x 128, 8 x 192 x 256 and
+    16 x 32 x 64 with a real V."""
+    torch = torch_cuda
+    import scipy.fft as sfft
+    from paper_2207_14222_gb300.solver import Solver
+    dev = torch.device("cuda:0")
+    cases = ((384,), False), ((96, 128), False), ((8, 192, 256), False), ((16, 32, 64), True)
+    for shape, vreal in cases:
+        if vreal:
+            cf, V, _ = _prep(inputs.random_diffusion(shape, 21), vreal=True)
+        else:
+            cf, V, _ = _prep(inputs.random_helmholtz(shape, 21))
+        Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+        x = inputs.random_field(shape, 22).astype(np.complex64)
+        x64, V64 = x.astype(np.complex128), V.astype(np.complex128)
+        y = uo.apply_A(x64, V64, Lh).astype(np.complex64)
+        y64 = y.astype(np.complex128)
+        ro = y64 - uo.apply_A(x64, V64, Lh)
+        rel_o = np.linalg.norm(ro) / np.linalg.norm(y64)
+        assert 1e-9 < rel_o < 1e-6, rel_o
+        # complex64 transforms cannot resolve it
+        r32 = y - (sfft.ifftn(Lh.astype(np.complex64) * sfft.fftn(x)) + V.astype(np.complex64) * x)
+        assert np.linalg.norm(r32 - ro) / np.linalg.norm(ro) > 0.1
+        with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), dx=cf["dx"],
+                    residual_fp64=fp64) as s:
+            r, rel = s.residual(torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev))
+        r = r.cpu().numpy()
+        assert np.linalg.norm(r - ro) / np.linalg.norm(ro) < 1e-3, shape
+        assert rel == pytest.approx(rel_o, rel=1e-3)
+
+
 # ------------------------------------------------------ edge cases ---
 
 def _solver(torch, shape, cf, V, **kw):
