@@ -282,6 +282,9 @@ struct SplitArgs {
   const float2* x_in;
   float2* x_out;
   const float2* y;      // bulk-copied rows: 16-byte aligned
+  const uint32_t* ymask;  // per rows tile u = 16 z + y2: bit y1 set when row
+                          // 16 y1 + y2 of plane z of y is not all zero (rows
+                          // left out are read as zeros); nullptr: every row
   const void* V;        // bulk-copied rows: 16-byte aligned
   float2* buf;          // scratch in the split layout
   const float2* tw;     // W_256^m table (device)
@@ -301,6 +304,9 @@ cudaError_t split_init();
 bool split_nz_ok(int nz);
 int split_cols_ctas_per_sm(int nz);
 cudaError_t launch_split_rows(int mode, const SplitArgs& a, int grid, cudaStream_t s);
+// mask[u] (nz * 16 words, u = 16 z + y2) = the rows of tile u in which y has
+// a value other than zero (NaN and Inf count as nonzero).
+cudaError_t launch_split_ymask(const float2* y, int nz, uint32_t* mask, cudaStream_t s);
 // map: the scratch viewed as 4-D {kx 256, z nz, y2 16, k1 16} (8-byte
 // elements, strides in that order 32768 / 2048 / nz * 32768 bytes), box {2, nz, 16, 1}.
 cudaError_t launch_split_cols(int nz, const CUtensorMap& map, const SplitColsArgs& a, int grid,

@@ -190,9 +190,12 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     }
     const bool real = which == 1 && vreal;
     const uint32_t rb = real ? SP_N * 4u : SP_N * 8u;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[which], SP_R1 * rb);
+    // rows of y that are all zero are not copied (the pointwise step reads
+    // them as zeros)
+    const uint32_t rows = which == 2 && a.ymask ? a.ymask[u] & 0xFFFFu : 0xFFFFu;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[which], __popc(rows) * rb);
     __syncwarp();
-    if (lane < SP_R1) {
+    if (lane < SP_R1 && ((rows >> lane) & 1u)) {
       const int64_t r = row_of(u, lane);
       const char* src = which == 1 ? reinterpret_cast<const char*>(a.V) + r * rb
                                    : reinterpret_cast<const char*>(a.y + r * SP_N);
@@ -247,6 +250,8 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     const int64_t u = tile_of(k);
     const int y2 = int(u & 15);
     const int64_t row = row_of(u, f);
+    // this thread's row of y was copied (else it is zero)
+    const bool yrow = !a.ymask || ((a.ymask[u] >> f) & 1u);
     float2 v[16];
     if (POST) {
       wait_bar(0, par);
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         const float2 xn = make_float2(xr[q].x + a.alpha * dr, xr[q].y + a.alpha * di);
         if (!ref) a.x_out[row * SP_N + g + 16 * q] = xn;
         if (PRE) {
-          const float2 yv = SY[cidx];
+          const float2 yv = yrow ? SY[cidx] : make_float2(0.f, 0.f);
           v[q] = make_float2(yv.x + br * xn.x - bi * xn.y, yv.y + br * xn.y + bi * xn.x);
         }
       }
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         const int cidx = f * SP_N + g + 16 * q;
         const float2 vv = vreal ? make_float2(reinterpret_cast<const float*>(SV)[cidx], 0.f) : SV[cidx];
         const float br = 1.f - vv.x, bi = -vv.y;
-        const float2 yv = SY[cidx];
+        const float2 yv = yrow ? SY[cidx] : make_float2(0.f, 0.f);
         v[q] = make_float2(yv.x + br * xr[q].x - bi * xr[q].y, yv.y + br * xr[q].y + bi * xr[q].x);
       }
       release_then(1, k + 1);
@@ -595,6 +600,29 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
   }
 }
 
+// ------------------------------------------------------ source row mask ---
+//
+// One warp per row of y (256 values, 2 KB): any value other than zero sets
+// bit y1 of its rows tile's word.  NaN compares unequal to zero, so a
+// non-finite source is always copied and reaches the iteration's check.
+__global__ void __launch_bounds__(256) k_split_ymask(const float4* y, int64_t nrows, uint32_t* mask) {
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  const float4* p = y + r * (SP_N / 2);
+  bool nz = false;
+#pragma unroll
+  for (int i = 0; i < SP_N / 2 / 32; ++i) {
+    const float4 v = __ldcs(p + lane + 32 * i);
+    nz = nz || v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f;
+  }
+  if (__any_sync(0xffffffffu, nz) && lane == 0) {
+    const int64_t z = r / SP_N;
+    const int yy = int(r % SP_N);
+    atomicOr(mask + z * SP_R2 + (yy % SP_R2), 1u << (yy / SP_R2));
+  }
+}
+
 // ----------------------------------------------------------- launchers ---
 
 static size_t split_rows_smem() { return sizeof(float2) * (3 * SA_TILE + 2 * SP_N); }
@@ -631,6 +659,14 @@ int split_cols_ctas_per_sm(int nz) {
     case 256: return SplitCols<256>::MINB;
     default: return 0;
   }
+}
+
+cudaError_t launch_split_ymask(const float2* y, int nz, uint32_t* mask, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (size_t)nz * SP_R2, s);
+  if (e != cudaSuccess) return e;
+  const int64_t nrows = (int64_t)nz * SP_N;
+  k_split_ymask<<<(unsigned)((nrows + 7) / 8), 256, 0, s>>>(reinterpret_cast<const float4*>(y), nrows, mask);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_rows(int mode, const SplitArgs& a, int grid, cudaStream_t s) {

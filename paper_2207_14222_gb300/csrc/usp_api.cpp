@@ -142,6 +142,9 @@ struct usp_solver {
   bool maps_ok = false;            // TMA tensor maps of the scratch field
   CUtensorMap map_ax[3][2];        // [tile 32 / 16 / 8 columns][axis]: strided-axis views of s->buf
   bool split_ok = false;           // split_map encoded (grids nz x 256 x 256)
+  uint32_t* ymask = nullptr;       // split layout: per rows tile, the rows where the source is nonzero
+  const float2* ymask_src = nullptr;  // the source the mask was last built from
+  double ymask_frac = 1.0;         // fraction of rows with a nonzero source (when counted)
   CUtensorMap split_map;           // the scratch in the split layout, 4-D (column-pass tiles)
 };
 
@@ -583,6 +586,7 @@ static SplitArgs split_args(usp_solver* s, const float2* y, const float2* xin, f
   a.x_in = xin;
   a.x_out = xout;
   a.y = y;
+  a.ymask = (y && y == s->ymask_src) ? s->ymask : nullptr;
   a.V = s->V;
   a.buf = s->buf;
   a.tw = s->tw32;
@@ -591,6 +595,30 @@ static SplitArgs split_args(usp_solver* s, const float2* y, const float2* xin, f
   a.hist = s->hist;
   a.alpha = (float)s->alpha;
   return a;
+}
+
+// The split rows pass copies only the rows of the source y that hold a
+// nonzero value (a point source or a beam on one face fills a few of the
+// grid's rows): build the row mask of y before a phase that iterates on it.
+// The mask is rebuilt at every phase start, so it always describes the
+// source's current contents.  With `count`, also the fraction of rows kept.
+static usp_status prepare_source_mask(usp_solver* s, const float2* y, bool count) {
+  if (!use_split(s, y)) return USP_OK;
+  const int nz = s->n[0];
+  if (!s->ymask) CUDA_TRY(cudaMalloc(&s->ymask, sizeof(uint32_t) * (size_t)nz * 16));
+  CUDA_TRY(launch_split_ymask(y, nz, s->ymask, s->stream));
+  g_launches.fetch_add(1);
+  s->ymask_src = y;
+  if (count) {
+    std::vector<uint32_t> m((size_t)nz * 16);
+    CUDA_TRY(cudaMemcpyAsync(m.data(), s->ymask, sizeof(uint32_t) * m.size(), cudaMemcpyDeviceToHost,
+                             s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    int64_t rows = 0;
+    for (uint32_t w : m) rows += __builtin_popcount(w & 0xFFFFu);
+    s->ymask_frac = (double)rows / (double)(nz * 256);
+  }
+  return USP_OK;
 }
 
 static std::function<cudaError_t(cudaStream_t)> split_rows_pass(usp_solver* s, int mode,
@@ -604,7 +632,8 @@ static std::vector<PassLaunch> split_prologue(usp_solver* s, const float2* y, co
   const double vb = s->vreal ? 4.0 : 8.0;
   const bool xz = (flags & F_XZERO) != 0;
   SplitArgs a = split_args(s, y, xin, nullptr, flags & ~F_REF);
-  return {{"split_rows_pre", 16.0 + (xz ? 0.0 : 8.0 + vb), split_rows_pass(s, SPLIT_PRE, a)}};
+  const double yb = 8.0 * (a.ymask ? s->ymask_frac : 1.0);   // source rows copied
+  return {{"split_rows_pre", 8.0 + yb + (xz ? 0.0 : 8.0 + vb), split_rows_pass(s, SPLIT_PRE, a)}};
 }
 
 static std::vector<PassLaunch> split_passes(usp_solver* s, const float2* y, const float2* xin,
@@ -625,7 +654,10 @@ static std::vector<PassLaunch> split_passes(usp_solver* s, const float2* y, cons
                [=](cudaStream_t t) { return launch_split_cols(nz, cmap, c, cgrid, t); }});
   SplitArgs a = split_args(s, y, xin, xout, flags);
   if (ref) P.push_back({"split_rows_post", 8.0 + vb, split_rows_pass(s, SPLIT_POST, a)});
-  else P.push_back({"split_rows_full", 32.0 + vb + (xz ? 0.0 : 8.0), split_rows_pass(s, SPLIT_FULL, a)});
+  else {
+    const double yb = 8.0 * (a.ymask ? s->ymask_frac : 1.0);   // source rows copied
+    P.push_back({"split_rows_full", 24.0 + yb + vb + (xz ? 0.0 : 8.0), split_rows_pass(s, SPLIT_FULL, a)});
+  }
   return P;
 }
 
@@ -762,6 +794,7 @@ static void destroy_impl(usp_solver* s) {
   cudaFreeHost(s->red_host);
   cudaFree(s->z);
   cudaFree(s->yp);
+  cudaFree(s->ymask);
   cudaFree(s->buf64);
   cudaFree(s->hy);
   cudaFree(s->hx);
@@ -1083,6 +1116,10 @@ static usp_status run_phase(usp_solver* s, const float2* y, float2* x, bool zero
     return USP_OK;
   }
   const int chunk = s->opt.chunk > 0 ? s->opt.chunk : 8;
+  {
+    usp_status st = prepare_source_mask(s, y, false);
+    if (st != USP_OK) return st;
+  }
   // the first iteration is launched directly (it may start from x = 0)
   {
     cudaError_t e = enqueue_iteration(s, y, x, x, zero_start ? F_XZERO : 0, s->stream, true, true);
@@ -1521,6 +1558,7 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
     h.tol = 0.0;
   }
   if ((st = write_state(s)) != USP_OK) return st;
+  if ((st = prepare_source_mask(s, (const float2*)y, true)) != USP_OK) return st;
   if (use_onchip(s)) {
     // one launch of `iters` iterations; its mean per iteration
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -190,3 +190,73 @@ def test_split_general_complex_symbol(torch_cuda):
     Lh = uo.lhat(shape, cf["dx"], a, b)
     xo, _ = uo.iterate(V.astype(np.complex128), y.astype(np.complex128), Lh, res["alpha"], n_iter)
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL_X
+
+
+def _sparse_rows_source(shape, seed, keep=0.1):
+    """A random source with all but a random tenth of its rows (x lines) set
+    to zero, so that tiles hold every mix of copied and skipped rows."""
+    rng = np.random.default_rng(seed)
+    prob = inputs.white_helmholtz(shape, seed)
+    rows = rng.uniform(size=shape[:-1]) < keep
+    rows[0, 0] = rows[-1, -1] = True
+    prob["S"] = prob["S"] * rows[..., None]
+    return prob, rows
+
+
+def test_split_source_row_mask(torch_cuda):
+    """The rows pass copies only the source rows that hold a nonzero value;
+    the others enter as zeros.  A source with 90% of its rows zero (random
+    rows, both ends set) follows the oracle, and the pass's byte count drops
+    by the skipped rows' 8 B per point."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (32, 256, 256)
+    prob, rows = _sparse_rows_source(shape, 58)
+    _check(torch, shape, prob, 20)
+    cf, V, y = _prep(prob)
+    assert np.array_equal(np.any(y != 0, axis=-1), rows)
+    dev = torch.device("cuda:0")
+    yd = torch.from_numpy(y).to(dev)
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), plain=True,
+                schedule=4) as s:
+        x = torch.zeros_like(yd)
+        s.solve(yd, x=x, tol=0.0, maxit=2)
+        passes = {p["name"]: p for p in s.time_passes(yd, x, iters=2)}
+    npts = int(np.prod(shape))
+    expect = (24.0 + 8.0 * rows.mean() + 8.0 + 8.0) * npts   # scratch, x, V (complex)
+    assert passes["split_rows_full"]["bytes"] == pytest.approx(expect, rel=1e-12)
+
+
+def test_split_source_mask_follows_the_source(torch_cuda):
+    """The mask is rebuilt from the source at every phase: the same device
+    buffer refilled with a different source between two solves gives the
+    second source's solution, and a NaN placed in a row that was zero
+    before is still reported."""
+    torch = torch_cuda
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (32, 256, 256)
+    prob1, _ = _sparse_rows_source(shape, 59, keep=0.02)
+    prob2, _ = _sparse_rows_source(shape, 60, keep=0.5)
+    cf1, V, y1 = _prep(prob1)
+    cf2 = ocanon.canonical(dict(prob2, k2=prob1["k2"]))
+    y2 = cf2["y"].astype(np.complex64)
+    dev = torch.device("cuda:0")
+    yd = torch.from_numpy(y1).to(dev)
+    n_iter = 20
+    with Solver(shape, cf1["a"], cf1["b"], torch.from_numpy(V).to(dev), plain=True,
+                schedule=4) as s:
+        s.solve(yd, tol=0.0, maxit=n_iter)
+        yd.copy_(torch.from_numpy(y2))
+        x, res = s.solve(yd, tol=0.0, maxit=n_iter)
+        xg = x.cpu().numpy().astype(np.complex128)
+        yb = y2.copy()
+        zero_rows = np.argwhere(~np.any(y2 != 0, axis=-1))
+        z, yy = zero_rows[len(zero_rows) // 2]
+        yb[z, yy, 7] = np.nan
+        yd.copy_(torch.from_numpy(yb))
+        with pytest.raises(_lib.UspError) as e:
+            s.solve(yd, tol=1e-6, maxit=10)
+        assert e.value.status == _lib.ERR_NONFINITE
+    Lh = uo.lhat(shape, cf1["dx"], cf1["a"], cf1["b"])
+    xo, _ = uo.iterate(V.astype(np.complex128), y2.astype(np.complex128), Lh, res["alpha"], n_iter)
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL_X
