@@ -511,10 +511,12 @@ typedef struct {
 } usp_pass_time;
 
 /* Run `iters` iterations of the solver's schedule on (y, x) -- device
- * pointers as in usp_solve; x is overwritten -- launching every kernel
- * directly with a CUDA event before and after it, and report per-kernel
- * mean durations.  out: host array of `capacity` entries; *n_out = number
- * of kernels per iteration. */
+ * pointers as in usp_solve; x is overwritten -- after one untimed
+ * iteration, launching every kernel directly and back to back with a CUDA
+ * event between consecutive kernels, and report per-kernel mean durations
+ * (device time between the kernel's neighbours' events; the host's launch
+ * latency is hidden behind the kernel before).  out: host array of
+ * `capacity` entries; *n_out = number of kernels per iteration. */
 usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int32_t iters,
                            usp_pass_time* out, int32_t capacity, int32_t* n_out);
 

@@ -421,6 +421,56 @@ __device__ __forceinline__ int zpos(int cbase, int c, int g, int q) {
   return colpos<NZ>(c, IN ? in_index<NZ>(g, q) : out_index<NZ>(g, q));
 }
 
+// x 1/(N (Lhat + 1)) on the spectrum of one z column (frequencies kxx,
+// ky; this thread's kz = out_index(g, q)), then the registers reordered for
+// the inverse transform.  Specialised for the Helmholtz form (a purely
+// imaginary: Re(Lhat + 1) constant) and real symbols (diffusion).
+template <int NZ>
+__device__ __forceinline__ void spectral_multiply(float2* v, const Sym<float>& sy, const float* pz2,
+                                                  float b1, int g, int kxx, int ky) {
+  constexpr int N1 = Split<NZ>::N1;
+  const float p2in = axis_p2(sy, 2, kxx) + axis_p2(sy, 1, ky);
+  if (sy.table) {
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const float2 l = sy.table[((int64_t)out_index<NZ>(g, q) * SP_N + ky) * SP_N + kxx];
+      const float dr = l.x + 1.f;
+      const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, l.y * l.y));
+      v[q] = cmul(v[q], make_float2(dr * sc, -l.y * sc));
+    }
+  } else if (sy.a_re == 0.f) {
+    // Helmholtz form: a purely imaginary, so Re(Lhat + 1) = Re b + 1
+    const float dr2 = b1 * b1;
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const float di = fmaf(sy.a_im, p2in + pz2[q], sy.b_im);
+      const float sc = __fdividef(sy.inv_n, fmaf(di, di, dr2));
+      v[q] = cmul(v[q], make_float2(b1 * sc, -di * sc));
+    }
+  } else if (sy.a_im == 0.f && sy.b_im == 0.f) {
+    // real symbol (diffusion): a real factor
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const float sc = __fdividef(sy.inv_n, fmaf(sy.a_re, p2in + pz2[q], b1));
+      v[q] = make_float2(v[q].x * sc, v[q].y * sc);
+    }
+  } else {
+    // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const float p2 = p2in + pz2[q];
+      const float dr = fmaf(sy.a_re, p2, b1);
+      const float di = fmaf(sy.a_im, p2, sy.b_im);
+      const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, di * di));
+      v[q] = cmul(v[q], make_float2(dr * sc, -di * sc));
+    }
+  }
+  float2 tmp[N1];
+  out_to_in<NZ>(v, tmp);
+#pragma unroll
+  for (int q = 0; q < N1; ++q) v[q] = tmp[q];
+}
+
 template <int NZ>
 __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     k_split_cols(const __grid_constant__ CUtensorMap cmap, const SplitColsArgs a) {
@@ -508,49 +558,7 @@ __global__ void __launch_bounds__(SplitCols<NZ>::THREADS, SplitCols<NZ>::MINB)
     for (int q = 0; q < N1; ++q) v[q] = T[zpos<NZ, true>(cbase, c, g, q)];
     __syncwarp();
     fft_line<NZ, false>(v, T + c * NZ, tws, g);
-    {
-      const int kxx = SP_XB * xb + (c & 1), ky = k1 + SP_R1 * (c >> 1);
-      const float p2in = axis_p2(sy, 2, kxx) + axis_p2(sy, 1, ky);
-      if (sy.table) {
-#pragma unroll
-        for (int q = 0; q < N1; ++q) {
-          const float2 l = sy.table[((int64_t)out_index<NZ>(g, q) * SP_N + ky) * SP_N + kxx];
-          const float dr = l.x + 1.f;
-          const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, l.y * l.y));
-          v[q] = cmul(v[q], make_float2(dr * sc, -l.y * sc));
-        }
-      } else if (sy.a_re == 0.f) {
-        // Helmholtz form: a purely imaginary, so Re(Lhat + 1) = Re b + 1
-        const float dr2 = b1 * b1;
-#pragma unroll
-        for (int q = 0; q < N1; ++q) {
-          const float di = fmaf(sy.a_im, p2in + pz2[q], sy.b_im);
-          const float sc = __fdividef(sy.inv_n, fmaf(di, di, dr2));
-          v[q] = cmul(v[q], make_float2(b1 * sc, -di * sc));
-        }
-      } else if (sy.a_im == 0.f && sy.b_im == 0.f) {
-        // real symbol (diffusion): a real factor
-#pragma unroll
-        for (int q = 0; q < N1; ++q) {
-          const float sc = __fdividef(sy.inv_n, fmaf(sy.a_re, p2in + pz2[q], b1));
-          v[q] = make_float2(v[q].x * sc, v[q].y * sc);
-        }
-      } else {
-        // 1 / (N (Lhat + 1)), Lhat = a |p|^2 + b
-#pragma unroll
-        for (int q = 0; q < N1; ++q) {
-          const float p2 = p2in + pz2[q];
-          const float dr = fmaf(sy.a_re, p2, b1);
-          const float di = fmaf(sy.a_im, p2, sy.b_im);
-          const float sc = __fdividef(sy.inv_n, fmaf(dr, dr, di * di));
-          v[q] = cmul(v[q], make_float2(dr * sc, -di * sc));
-        }
-      }
-      float2 tmp[N1];
-      out_to_in<NZ>(v, tmp);
-#pragma unroll
-      for (int q = 0; q < N1; ++q) v[q] = tmp[q];
-    }
+    spectral_multiply<NZ>(v, sy, pz2, b1, g, SP_XB * xb + (c & 1), k1 + SP_R1 * (c >> 1));
     fft_line<NZ, true>(v, T + c * NZ, tws, g);
 #pragma unroll
     for (int q = 0; q < N1; ++q) T[zpos<NZ, false>(cbase, c, g, q)] = v[q];

@@ -1553,7 +1553,7 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
   for (int p = 0; p < s->B; ++p) {
     DevState& h = s->st_host[p];
     std::memset(&h, 0, sizeof h);
-    h.it_limit = use_onchip(s) ? iters : iters + 1;  // on-chip: one launch runs them all
+    h.it_limit = use_onchip(s) ? iters : iters + 2;  // on-chip: one launch runs them all
     h.ref = 1.0;   // fixed denominator: nothing stops the timed iterations
     h.tol = 0.0;
   }
@@ -1591,28 +1591,41 @@ extern "C" usp_status usp_time_passes(usp_solver* s, const void* y, void* x, int
   }
   auto passes = iteration_passes(s, (const float2*)y, (const float2*)x, (float2*)x, 0);
   const size_t np = passes.size();
-  std::vector<cudaEvent_t> ev(2 * np, nullptr);
-  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
-  std::vector<double> acc(np, 0.0);
+  // One untimed iteration goes first, and the timed ones are queued back to
+  // back with one event between consecutive launches: each launch is then
+  // already waiting when the event before it completes, so the events
+  // bracket device time only, not the host's launch latency.
+  std::vector<cudaEvent_t> ev((size_t)iters * np + 1, nullptr);
   usp_status res = USP_OK;
+  for (auto& e : ev)
+    if (res == USP_OK && cudaEventCreate(&e) != cudaSuccess) res = fail(USP_ERR_CUDA, "event create");
+  std::vector<double> acc(np, 0.0);
+  for (size_t k = 0; k < np && res == USP_OK; ++k) {
+    if (passes[k].go(s->stream) != cudaSuccess) res = fail(USP_ERR_CUDA, "timing launch");
+    g_launches.fetch_add(1);
+  }
+  if (res == USP_OK && cudaEventRecord(ev[0], s->stream) != cudaSuccess)
+    res = fail(USP_ERR_CUDA, "timing event");
   for (int it = 0; it < iters && res == USP_OK; ++it) {
     for (size_t k = 0; k < np; ++k) {
-      cudaError_t e = cudaEventRecord(ev[2 * k], s->stream);
-      if (e == cudaSuccess) e = passes[k].go(s->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], s->stream);
+      cudaError_t e = passes[k].go(s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)it * np + k + 1], s->stream);
       if (e != cudaSuccess) { res = fail(USP_ERR_CUDA, "timing launch: %s", cudaGetErrorString(e)); break; }
       g_launches.fetch_add(1);
     }
-    if (res != USP_OK) break;
+  }
+  if (res == USP_OK) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) { res = fail(USP_ERR_CUDA, "timing sync: %s", cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) res = fail(USP_ERR_CUDA, "timing sync: %s", cudaGetErrorString(e));
+  }
+  for (int it = 0; it < iters && res == USP_OK; ++it)
     for (size_t k = 0; k < np; ++k) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+      cudaEventElapsedTime(&ms, ev[(size_t)it * np + k], ev[(size_t)it * np + k + 1]);
       acc[k] += ms;
     }
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
   if (res == USP_OK) {
     const int m = std::min<int>((int)np, std::max(0, (int)capacity));
     for (int k = 0; k < m; ++k) {
