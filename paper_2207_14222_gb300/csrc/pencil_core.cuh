@@ -45,10 +45,12 @@ template <> struct RowsCfg<double> {
   static constexpr int THREADS = 128;
   static constexpr int MINB = 1;
 };
-// double-float (the refinement residual): the same register footprint as FP64
+// double-float (the refinement residual): the FP64 block shape (same row
+// blocks), at four blocks per SM -- the 256-point pass fits 128 registers
+// without spilling, and twice the warps hide its global loads
 template <> struct RowsCfg<dfl> {
   static constexpr int THREADS = 128;
-  static constexpr int MINB = 1;
+  static constexpr int MINB = 4;
 };
 // Block shape of the line pass for lines of length N: radix-3 lines use
 // 3/4 of the threads so that whole lines fill a block.
