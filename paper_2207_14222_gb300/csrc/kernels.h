@@ -264,6 +264,7 @@ cudaError_t rows_tma_init();
 // Rows per tile of the staged rows pass for rows of length n (0: no staged
 // kernel for this length).
 int rows_tma_tile_rows(int n);
+int rows_tma_ctas_per_sm(int n);
 cudaError_t launch_rows_tma(int n, const RowsTmaArgs& a, int grid, cudaStream_t s);
 
 // Split-y two-pass schedule (split3d_kernels.cu), grids nz x 256 x 256 with

@@ -62,10 +62,13 @@ struct RowsShape {
   static constexpr int MINB = N >= 384 && RowsCfg<T>::MINB > 2 ? 2 : RowsCfg<T>::MINB;
   static_assert(F * Line<N>::G == THREADS, "lines must fill the block");
 };
-// Columns per block of the strided-axis pass (lanes per line thread).
+// Columns per block of the strided-axis pass (lanes per line thread):
+// 512-point lines 8 (113 against 119 us with 16, one pass over a batch of 68
+// problems of 512^2), 96- and 192-point lines 16 (24.6 against 28.6 us with
+// 32 on 70 problems of 192^2), 384-point lines 16 (8: 72 against 70 us).
 template <int N>
 struct ColsShape {
-  static constexpr int COLS = N >= 384 ? 16 : 32;
+  static constexpr int COLS = N == 512 ? 8 : (N % 3 == 0 ? 16 : 32);
   static constexpr int THREADS = COLS * Line<N>::G;
 };
 

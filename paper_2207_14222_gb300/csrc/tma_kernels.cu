@@ -281,11 +281,18 @@ __device__ __forceinline__ void fft_rows_slot(float2* v, float2* exr, const floa
   for (int q = 0; q < N1; ++q) v[q] = w[q];
 }
 
-// Block shape of the staged rows pass: G line threads per row (Line<N>),
-// 512 threads (384 for radix-3 lines, so that whole rows fill the block).
+// Block shape of the staged rows pass: G line threads per row (Line<N>).
+// Lines of 256 points and more: 256 threads (192 for radix-3 lines, so that
+// whole rows fill the block), tiles of 8 rows, two CTAs per SM -- measured
+// on batches of 2-D problems against one CTA of twice the threads: 512
+// points 175 vs 208 us, 384 points 115 vs 131 us, 256 points 56 vs 60 us,
+// and the 3-D pencil rows pass at 256^3 124 vs 126 us.  Shorter lines: 512
+// threads in one CTA per SM.
 template <int N>
 struct RowsTma {
-  static constexpr int THREADS = Line<N>::R == 3 ? 384 : 512;
+  static constexpr bool LONG = N >= 256;
+  static constexpr int THREADS = (Line<N>::R == 3 ? 384 : 512) / (LONG ? 2 : 1);
+  static constexpr int MINB = LONG ? 2 : 1;
   static constexpr int F = THREADS / Line<N>::G;   // rows per tile
   static_assert(F * Line<N>::G == THREADS, "rows must fill the block");
 };
@@ -309,7 +316,7 @@ __device__ __forceinline__ void line_fwd_slot(float2* v, float2* exr, const floa
 }
 
 template <int N>
-__global__ void __launch_bounds__(RowsTma<N>::THREADS, 1) k_rows_tma(const RowsTmaArgs a) {
+__global__ void __launch_bounds__(RowsTma<N>::THREADS, RowsTma<N>::MINB) k_rows_tma(const RowsTmaArgs a) {
   typedef Line<N> L;
   constexpr int N1 = L::NV, G = L::G, M = L::M;
   constexpr int THREADS = RowsTma<N>::THREADS;
@@ -559,6 +566,16 @@ cudaError_t rows_tma_init() {
   if ((e = rows_tma_attr<256>()) != cudaSuccess) return e;
   if ((e = rows_tma_attr<384>()) != cudaSuccess) return e;
   return rows_tma_attr<512>();
+}
+
+int rows_tma_ctas_per_sm(int n) {
+  switch (n) {
+    case 128: return RowsTma<128>::MINB;
+    case 256: return RowsTma<256>::MINB;
+    case 384: return RowsTma<384>::MINB;
+    case 512: return RowsTma<512>::MINB;
+    default: return 1;
+  }
 }
 
 int rows_tma_tile_rows(int n) {

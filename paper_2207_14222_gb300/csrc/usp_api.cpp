@@ -431,7 +431,7 @@ static std::vector<PassLaunch> pencil_passes(usp_solver* s, const float2* y, con
       t.alpha = (float)s->alpha;
       t.bt = r.bt;
       const int64_t tiles = (r.nrows + tile_rows - 1) / tile_rows;
-      const int tgrid = (int)std::min<int64_t>(tiles, s->num_sms);
+      const int tgrid = (int)std::min<int64_t>(tiles, (int64_t)s->num_sms * rows_tma_ctas_per_sm(nx));
       P.push_back({"rows_inv_post_pre_fwd", bytes,
                    [=](cudaStream_t st) { return launch_rows_tma(nx, t, tgrid, st); }});
     } else {
@@ -917,8 +917,8 @@ static usp_status create_impl(const usp_grid* grid, int count, const usp_lsymbol
   CREATE_TRY(cudaMalloc(&s->buf, sizeof(float2) * (size_t)NB));
   const int64_t g32 = rows_grid_f32(s), g64 = rows_grid_f64(s);
   // one per block of the rows passes, two per FP64 block, one per tile
-  // (at least 16 lines) of the staged rows pass, three per statistics block
-  s->npartials = std::max<int64_t>({g32, 2 * g64, NB / s->n[s->ndim - 1] / 16 + 1, 3 * 1024, 64});
+  // (at least 8 lines) of the staged rows pass, three per statistics block
+  s->npartials = std::max<int64_t>({g32, 2 * g64, NB / s->n[s->ndim - 1] / 8 + 1, 3 * 1024, 64});
   CREATE_TRY(cudaMalloc(&s->partials, sizeof(double) * s->npartials));
   CREATE_TRY(cudaMalloc(&s->st, sizeof(DevState) * count));
   CREATE_TRY(cudaMallocHost(&s->st_host, sizeof(DevState) * count));

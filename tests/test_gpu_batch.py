@@ -84,6 +84,8 @@ def _check_trajectories(torch, shape, probs, n_iter, vreal=False, schedule=0):
     ((96, 96), 3, 0),          # on-chip, radix-3 lines
     ((192, 192), 2, 0),
     ((512, 64), 2, 0),         # radix-2 outer stage on the strided axis
+    ((16, 512), 3, 1),         # staged 512-point line pass, two 8-row tiles per problem
+    ((32, 384), 2, 1),         # staged 384-point line pass, four 8-row tiles per problem
     ((64, 64), 5, 0),          # on-chip: one cluster per problem
     ((128, 128), 3, 0),
     ((256, 256), 2, 0),
