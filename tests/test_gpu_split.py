@@ -8,8 +8,11 @@ oracle's Algorithm 1 on the same complex64 (or float32) inputs, at the
 complex64 bar (rel-L2 1e-5 on x, 1e-4 on the residual history).
 """
 
+import os
+
 import numpy as np
 import pytest
+import scipy.fft as sfft
 
 from oracle import canon as ocanon
 from oracle import usp_oracle as uo
@@ -55,7 +58,10 @@ def _check(torch, shape, prob, n_iter, vreal=False, **opts):
     Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
     V64, y64 = V.astype(np.complex128), y.astype(np.complex128)
     assert res["alpha"] == pytest.approx(uo.alpha_star(V64), rel=1e-6)
-    xo, ho = uo.iterate(V64, y64, Lh, res["alpha"], n_iter)
+    # the oracle's transform on every host core (its arithmetic does not
+    # depend on the worker count)
+    with sfft.set_workers(os.cpu_count() or 1):
+        xo, ho = uo.iterate(V64, y64, Lh, res["alpha"], n_iter)
     err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
     assert err <= TOL_X, err
     far = ho > 1e-3
@@ -79,15 +85,18 @@ def test_split_parity_real_potential(torch_cuda):
 
 
 def test_split_parity_full_size_helmholtz(torch_cuda):
-    """The benchmark's workload (3-D Helmholtz 256^3) on the split schedule,
-    every output compared with the oracle after 3 iterations."""
+    """The benchmark's workload (3-D Helmholtz 256^3, a beam source in one
+    plane, so the rows pass copies 0.4% of the source rows) on the split
+    schedule, every output compared with the oracle after 20 iterations."""
     shape = (256, 256, 256)
-    _check(torch_cuda, shape, inputs.helmholtz_3d(256, seed=0), 3)
+    _check(torch_cuda, shape, inputs.helmholtz_3d(256, seed=0), 20)
 
 
 def test_split_parity_full_size_diffusion(torch_cuda):
+    """The 3-D diffusion workload (real V, a point source) after 20
+    iterations."""
     shape = (256, 256, 256)
-    _check(torch_cuda, shape, inputs.diffusion_3d(256, seed=0), 3, vreal=True)
+    _check(torch_cuda, shape, inputs.diffusion_3d(256, seed=0), 20, vreal=True)
 
 
 def test_split_and_pencil_schedules_agree(torch_cuda):
