@@ -449,6 +449,31 @@ def test_refinement_residual_below_fp32_rounding(torch_cuda, fp64):
         assert rel == pytest.approx(rel_o, rel=1e-3)
 
 
+def test_refinement_residual_full_size(torch_cuda):
+    """The refinement residual at the benchmark's size (3-D Helmholtz 256^3,
+    double-float arithmetic, the automatic schedule's solver): y = A x up to
+    complex64 rounding, r within 1e-3 of the FP64 oracle's."""
+    torch = torch_cuda
+    import os
+    import scipy.fft as sfft
+    from paper_2207_14222_gb300.solver import Solver
+    shape = (256, 256, 256)
+    cf, V, _ = _prep(inputs.helmholtz_3d(256, seed=0))
+    Lh = uo.lhat(shape, cf["dx"], cf["a"], cf["b"])
+    x = inputs.random_field(shape, 23).astype(np.complex64)
+    x64, V64 = x.astype(np.complex128), V.astype(np.complex128)
+    with sfft.set_workers(os.cpu_count() or 1):
+        y = uo.apply_A(x64, V64, Lh).astype(np.complex64)
+        y64 = y.astype(np.complex128)
+        ro = y64 - uo.apply_A(x64, V64, Lh)
+    dev = torch.device("cuda:0")
+    with Solver(shape, cf["a"], cf["b"], torch.from_numpy(V).to(dev), dx=cf["dx"]) as s:
+        r, rel = s.residual(torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev))
+    r = r.cpu().numpy()
+    assert np.linalg.norm(r - ro) / np.linalg.norm(ro) < 1e-3
+    assert rel == pytest.approx(np.linalg.norm(ro) / np.linalg.norm(y64), rel=1e-3)
+
+
 # ------------------------------------------------------ edge cases ---
 
 def _solver(torch, shape, cf, V, **kw):
