@@ -407,6 +407,10 @@ def extras_legs(args, torch, dev, cf, V, y, shape, Solver, ref_iters):
         }
         out["roofline"].update(schedule_efficiency(passes, int(np.prod(shape)), V.dtype == torch.float32,
                                                    per_it_ms, peak))
+        if dom["name"] == "split_rows_full":
+            out["roofline"]["bytes_note"] = (
+                "split_rows_full reads only the source rows that hold nonzero values: 40 B/pt "
+                "(36 with a real V) plus 8 B/pt per nonzero source row; 48 B/pt with a dense source")
     # end to end through the host API: pinned V, y in; x out
     Vh = V.cpu().pin_memory()
     yh = y.cpu().pin_memory()
